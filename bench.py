@@ -1,0 +1,297 @@
+#!/usr/bin/env python3
+"""Seam-carving benchmark: seams/s of the GB300 path on the 1920x1080 -> 1440 workload.
+
+A step is one whole carve of the workload image: e1 energy once, then per seam the DP search
+(fill, argmin, backtrack), local energy refresh and row compaction, all on the GPU through the C
+ABI. Inputs are resident in HBM when timing starts; L2 is flushed (256 MB write) between steps,
+outside the per-step CUDA-event brackets. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Multi-GPU: every rank carves its own copy (replicas, weak scaling); value = all ranks' seams /
+the slowest rank's time. ``--impl reference`` times the oracle (plain C, host cores) on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--plain", action="store_true", help="time the per-seam-launch plain path")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _traffic_from_profile():
+    """Per-launch DRAM bytes of the DP kernel from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "k_dp_1920x1080.txt")
+    try:
+        with open(path) as f:
+            for ln in f:
+                if ln.startswith("dram_bytes_per_launch:"):
+                    return float(ln.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for ln in f:
+                    parts = [p.strip() for p in ln.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        finally:
+            if self.path:
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _workload():
+    from paper_2410_21207_gb300 import synth
+    return synth.config2()
+
+
+def cpu_baseline(job, img, budget_s: float = 15.0):
+    """The oracle (plain single-threaded C) on a bounded prefix of the workload's seams."""
+    import oracle
+    W, H = job.W, job.H
+    t0 = time.perf_counter()
+    oracle.carve(img, W - 2, H)
+    per = (time.perf_counter() - t0) / 2
+    n = max(2, min(W - job.target_w, int(budget_s / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.carve(img, W - n, H)
+    dt = time.perf_counter() - t0
+    mpix = sum(H * (W - t) for t in range(n)) / 1e6
+    return {"value": n / dt, "unit": "seams/s", "mpix_seam_per_s": mpix / dt, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} of {W - job.target_w} seams of the {W}x{H} workload, single-threaded C, "
+                      f"full energy recompute per seam"}
+
+
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    job = _workload()
+    img = job.make()
+    import oracle
+    W, H = job.W, job.H
+    t0 = time.perf_counter()
+    oracle.carve(img, W - 2, H)
+    per = (time.perf_counter() - t0) / 2
+    n = max(2, min(W - job.target_w, int(20.0 / max(a.steps, 1) / max(per, 1e-6))))
+    for _ in range(a.warmup):
+        oracle.carve(img, W - 1, H)
+    times = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        oracle.carve(img, W - n, H)
+        times.append(time.perf_counter() - t0)
+    dt = sum(times)
+    value = n * a.steps / dt
+    line = {
+        "impl": "reference", "metric": "seams/s", "value": value, "unit": "seams/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * dt / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"{job.name}; each step = the first {n} seams (bounded sample)",
+                   "parallelism": "single-threaded CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": "seams/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {n} of {W - job.target_w} seams per step"},
+        "e2e": {"value": value, "unit": "seams/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(a):
+    import numpy as np
+    import torch
+
+    from paper_2410_21207_gb300 import binding as sc
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    job = _workload()
+    img_np = job.make()
+    H, W, tw, th = job.H, job.W, job.target_w, job.target_h
+    seams = (W - tw) + (H - th)
+    mpix = job.mpix_seams()
+    img = torch.from_numpy(img_np).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        return sc.carve(img, tw, th, plain=a.plain)
+
+    for _ in range(max(a.warmup, 3)):
+        step()
+    sc.check()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    sc.timing_reset()
+    barrier()
+    with ClockSampler(local if ws > 1 else 0) as clk:
+        sc.timing_enable(True)
+        for k in range(a.steps):
+            flush.zero_()
+            starts[k].record()
+            step()
+            ends[k].record()
+        barrier()
+        sc.timing_enable(False)
+    sc.check()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    dp_ms, dp_n = sc.timing_read("dp")
+    _, launches = sc.timing_read("all")
+    total_s = sum(step_ms) / 1000.0
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = seams * a.steps * ws / total_s
+
+    # roofline of the dominant kernel (the DP seam search): algorithmic bytes = H*W_cur*2.25 per launch
+    dp_bytes = 2.25 * sum(H * (W - t) for t in range(W - tw)) + 2.25 * sum(tw * (H - t) for t in range(H - th))
+    dp_bytes_per_launch = dp_bytes / max(seams, 1)
+    achieved = (dp_bytes * a.steps) / (dp_ms / 1000.0) / 1e9 if dp_ms > 0 else None
+    peak, peak_src = _peaks()
+    traffic = _traffic_from_profile()
+
+    line = {
+        "metric": "seams/s", "value": value, "unit": "seams/s", "n_gpus": ws, "steps": a.steps,
+        "warmup": max(a.warmup, 3), "ms_per_step": 1000.0 * total_s / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": job.name + (" [plain path]" if a.plain else ""), "seams_per_step": seams,
+                   "mpix_seam_per_step": round(mpix, 1), "image": f"{W}x{H} RGB uint8 (synthetic generator G, seed 2)",
+                   "l2": "flushed between steps (256 MB write), outside the timed brackets",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "mpix_seam_per_s": mpix * a.steps * ws / total_s,
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "k_dp (seam search)", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "peak_source": peak_src, "dp_ms_per_launch": dp_ms / max(dp_n, 1),
+                     "algorithmic_bytes_per_launch": dp_bytes_per_launch},
+        "clocks": clk.summary(),
+    }
+
+    if rank == 0 and not a.no_e2e:
+        pinned = torch.from_numpy(img_np).pin_memory()
+        host_in = pinned.numpy()
+        t_e2e = []
+        for k in range(max(2, a.steps)):
+            t0 = time.perf_counter()
+            sc.carve_host(host_in, tw, th)
+            t_e2e.append(time.perf_counter() - t0)
+        e2e_s = statistics.median(t_e2e[1:]) if len(t_e2e) > 1 else t_e2e[0]
+        line["e2e"] = {"value": seams / e2e_s, "unit": "seams/s", "h2d_bytes_per_step": H * W * 3,
+                       "d2h_bytes_per_step": th * tw * 3}
+    if rank == 0 and not a.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(job, img_np)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_native(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

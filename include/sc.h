@@ -1,0 +1,147 @@
+/*
+ * sc.h — C ABI of the GB300 (sm_103a) seam-carving library libsc_gb300.so.
+ *
+ * The operations follow arXiv 2410.21207 ("Analysis of Different Algorithmic Design Techniques
+ * for Seam Carving"): the e1 energy (section "Energy Mapping"), the minimum vertical seam by the
+ * dynamic-programming recurrence M(i,j) = e(i,j) + min(M(i-1,j-1), M(i-1,j), M(i-1,j+1))
+ * (section "DP Seam Carving", Algorithm 3), removal of the seam by shifting each row left past it
+ * (section "Removal of Seams"), and horizontal seams as vertical seams of the transposed image
+ * (section "Design Techniques"). Integer arithmetic throughout:
+ *   - images are uint8, H rows x W columns x C channels, row-major (HWC), C in {1, 3, 4};
+ *   - e(i,j) = sum over channels of |I(i,j+1)-I(i,j-1)| + |I(i+1,j)-I(i-1,j)|, neighbour indices
+ *     clamped to the image (edge replication); e <= 2*255*C fits uint16;
+ *   - M is exact (int32 range); M(0,j) = e(0,j); neighbours outside the image are excluded;
+ *   - ties: the leftmost of (j-1, j, j+1) wins, and the leftmost minimum of the last row wins;
+ *   - a seam is int32 seam[H], seam[i] = its column in row i, in the coordinates of the image it
+ *     was found in.
+ * These fix one unique answer, so every seam and every output byte is reproducible bit for bit.
+ *
+ * Conventions for every entry point:
+ *   - Pointers are DEVICE pointers owned by the caller unless the name ends in _host. The library
+ *     never frees or keeps them after the call's work has finished on `stream`.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Work is
+ *     enqueued asynchronously on it; argument errors are returned synchronously, before any work
+ *     is enqueued.
+ *   - The library owns internal scratch (a workspace per (device, stream), grown on demand with
+ *     cudaMalloc and kept until sc_release_workspaces or exit). Calls on the same stream reuse it
+ *     in order; calls on different streams use different workspaces.
+ *   - Errors detected on the device (a failed internal consistency check, a bounded wait that
+ *     ran out) are recorded in the workspace and reported by sc_check(stream), which waits for
+ *     the stream.
+ *   - Return value: SC_OK (0) or a negative sc_status. sc_last_error() describes the last failure
+ *     of the calling thread.
+ *   - Limits: 1 <= H, W; H <= SC_MAX_ROWS rows for a seam search (cost fits 24 bits with headroom
+ *     for C = 4); W <= SC_MAX_COLS; H*W*C < 2^31.
+ */
+#ifndef SC_GB300_H
+#define SC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SC_OK = 0,
+  SC_EINVAL = -1,    /* bad argument (null pointer, size out of range, enlargement) */
+  SC_ENOMEM = -2,    /* device or host allocation failed */
+  SC_ECUDA = -3,     /* a CUDA runtime call failed (message in sc_last_error) */
+  SC_ETIMEOUT = -4,  /* a bounded device-side wait ran out; the context is still usable */
+  SC_EBUSY = -5,     /* a serving queue is full */
+  SC_EINTERNAL = -6  /* a device-side consistency check failed */
+} sc_status;
+
+#define SC_MAX_ROWS 8192
+#define SC_MAX_COLS 8192
+
+/* Library version (major*10000 + minor*100 + patch). */
+int sc_version(void);
+
+/* Message for the last failing call on this thread (static storage, never NULL). */
+const char *sc_last_error(void);
+
+/* Wait for `stream` and report device-side errors recorded by earlier calls on it (and clear
+ * them). Returns SC_OK, SC_EINTERNAL, SC_ETIMEOUT or SC_ECUDA. */
+int sc_check(void *stream);
+
+/* Free every workspace the library holds for the current device (after synchronising it). */
+int sc_release_workspaces(void);
+
+/* ---- instrumentation (no counterpart in the paper) ----
+ * sc_timing_enable(1) makes the library bracket every launch of the named kernels with CUDA
+ * events on the launching stream and count every kernel launch it makes; sc_timing_read waits
+ * for the recorded events and returns the summed device time (ms) and launch count of one kernel
+ * ("dp", "patch", "shift", "energy", "transpose", "pack", "unpack", "carve_batch") or, for
+ * kernel = "all", the total number of kernel launches (total_ms = 0). sc_timing_reset clears the
+ * records. Off by default; meant for benchmarks, not for concurrent use from several threads. */
+int sc_timing_enable(int on);
+int sc_timing_reset(void);
+int sc_timing_read(const char *kernel, double *total_ms, int64_t *launches);
+
+/* ---- e1 energy (section "Energy Mapping", item e1) ----
+ * img:        device, H x W x C uint8, row-major.
+ * energy_out: device, H x W uint16, row-major; written completely.
+ * Errors: SC_EINVAL if a pointer is NULL, H < 1, W < 1, C not in {1,3,4} or H*W*C >= 2^31. */
+int sc_energy(const uint8_t *img, int H, int W, int C, uint16_t *energy_out, void *stream);
+
+/* ---- one minimum vertical seam (section "DP Seam Carving", Algorithm 3, with the readings in
+ * the header comment) ----
+ * energy:   device, H x W uint16, row-major (any values; the sum along a seam must stay below
+ *           2^24, which H <= SC_MAX_ROWS guarantees for energies <= 2040).
+ * seam_out: device, int32[H]; seam_out[i] in [0, W), |seam_out[i] - seam_out[i-1]| <= 1.
+ * cost_out: device, int64[1] or NULL: the seam's total energy (the minimum of M's last row).
+ * Errors: SC_EINVAL for NULL energy/seam_out, H < 1, W < 1, H > SC_MAX_ROWS, W > SC_MAX_COLS,
+ *         or energies that could overflow (checked on the device: SC_EINTERNAL via sc_check). */
+int sc_find_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_t *cost_out, void *stream);
+
+/* ---- carve: remove (W - target_w) vertical seams, then (H - target_h) horizontal seams (found
+ * as vertical seams of the transposed image), recomputing the energy where the removal changed
+ * it (sections "Removal of Seams" and "Design Techniques"). The result equals: for each seam,
+ * recompute the full e1 energy, find the Algorithm 3 seam, delete it.
+ * img:      device, H x W x C uint8 (not modified).
+ * out:      device, target_h x target_w x C uint8.
+ * seam_log: device int32 or NULL. When given it receives (W - target_w) vertical seams of H
+ *           entries each (in the coordinates of the image each was found in), followed by
+ *           (H - target_h) horizontal seams of target_w entries each (in the transposed frame:
+ *           entry r is the row removed from column r).
+ * cost_log: device int64 or NULL: one cost per removed seam, in the same order.
+ * Errors: SC_EINVAL for NULL img/out, C not in {1,3,4}, target_w < 1, target_h < 1,
+ *         target_w > W or target_h > H (no enlargement), H or W above the limits. */
+int sc_carve(const uint8_t *img, int H, int W, int C, int target_w, int target_h, uint8_t *out,
+             int32_t *seam_log, int64_t *cost_log, void *stream);
+
+/* Same result as sc_carve, computed by the plain path: one image at a time with separate kernel
+ * launches for every seam (find, refresh, compact), no persistent kernel and no graph. It is the
+ * baseline the persistent/batched forms are measured against. Same arguments and errors. */
+int sc_carve_plain(const uint8_t *img, int H, int W, int C, int target_w, int target_h, uint8_t *out,
+                   int32_t *seam_log, int64_t *cost_log, void *stream);
+
+/* sc_carve with HOST buffers: img (H*W*C bytes) and out (target_h*target_w*C bytes) are host
+ * pointers (pinned memory is fastest); the call copies in, carves and copies out on `stream`, and
+ * returns after the result is in `out` (it synchronises the stream). Device errors are returned
+ * directly. Same limits as sc_carve. */
+int sc_carve_host(const uint8_t *img_host, int H, int W, int C, int target_w, int target_h, uint8_t *out_host,
+                  void *stream);
+
+/* ---- batched form: many images of uneven sizes carved by one persistent launch ----
+ * Each descriptor names one image; all pointers are device pointers. Images are processed
+ * independently and each result equals sc_carve on that image alone. */
+typedef struct {
+  const uint8_t *img;   /* H x W x C uint8 */
+  uint8_t *out;         /* target_h x target_w x C uint8 */
+  int32_t *seam_log;    /* NULL or as in sc_carve */
+  int H, W, C;
+  int target_w, target_h;
+  int reserved;
+} sc_image_desc;
+
+/* descs: HOST array of n descriptors (copied during the call). Errors: SC_EINVAL if n < 1,
+ * descs is NULL or any descriptor fails the sc_carve checks (nothing is enqueued then). */
+int sc_carve_batch(const sc_image_desc *descs, int n, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SC_GB300_H */

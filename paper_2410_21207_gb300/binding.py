@@ -1,0 +1,218 @@
+"""Thin Python binding of libsc_gb300 (include/sc.h): argument marshalling only.
+
+Every step of the seam-carving path runs in the library's CUDA kernels; PyTorch only provides
+device memory and the current stream. There is no CPU fallback: if the library is missing or no
+GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_lock = threading.Lock()
+
+SC_OK, SC_EINVAL, SC_ENOMEM, SC_ECUDA, SC_ETIMEOUT, SC_EBUSY, SC_EINTERNAL = 0, -1, -2, -3, -4, -5, -6
+MAX_ROWS = 8192
+MAX_COLS = 8192
+
+
+class ScError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sc status {code}: {msg}")
+        self.code = code
+
+
+class ImageDesc(ctypes.Structure):
+    _fields_ = [
+        ("img", ctypes.c_void_p), ("out", ctypes.c_void_p), ("seam_log", ctypes.c_void_p),
+        ("H", ctypes.c_int), ("W", ctypes.c_int), ("C", ctypes.c_int),
+        ("target_w", ctypes.c_int), ("target_h", ctypes.c_int), ("reserved", ctypes.c_int),
+    ]
+
+
+def header_functions() -> List[str]:
+    """Names of the functions include/sc.h declares."""
+    with open(os.path.join(_build.INCLUDE, "sc.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(sc_\w+)\s*\(", text, flags=re.M)))
+
+
+def load(path: Optional[str] = None):
+    """Load the shared library (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or _build.build()
+            lib = ctypes.CDLL(p)
+            P, I = ctypes.c_void_p, ctypes.c_int
+            sig = {
+                "sc_version": ([], I),
+                "sc_last_error": ([], ctypes.c_char_p),
+                "sc_check": ([P], I),
+                "sc_release_workspaces": ([], I),
+                "sc_energy": ([P, I, I, I, P, P], I),
+                "sc_find_seam": ([P, I, I, P, P, P], I),
+                "sc_carve": ([P, I, I, I, I, I, P, P, P, P], I),
+                "sc_carve_plain": ([P, I, I, I, I, I, P, P, P, P], I),
+                "sc_carve_host": ([P, I, I, I, I, I, P, P], I),
+                "sc_carve_batch": ([P, I, P], I),
+                "sc_timing_enable": ([I], I),
+                "sc_timing_reset": ([], I),
+                "sc_timing_read": ([ctypes.c_char_p, P, P], I),
+            }
+            for name, (args, res) in sig.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def _raise(code: int):
+    if code != SC_OK:
+        raise ScError(code, load().sc_last_error().decode())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libsc_gb300 needs a CUDA GPU; none is available")
+    return torch
+
+
+def _stream(torch, device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _img_shape(img) -> Tuple[int, int, int]:
+    if img.dim() == 2:
+        return img.shape[0], img.shape[1], 1
+    if img.dim() != 3:
+        raise ValueError("image must be H x W or H x W x C")
+    return img.shape[0], img.shape[1], img.shape[2]
+
+
+def _check_device_u8(img):
+    if img.device.type != "cuda" or str(img.dtype) != "torch.uint8" or not img.is_contiguous():
+        raise ValueError("image must be a contiguous uint8 CUDA tensor")
+
+
+def version() -> int:
+    return load().sc_version()
+
+
+def check(device=None) -> None:
+    """Wait for the current stream and raise if a device-side check failed."""
+    torch = _torch()
+    _raise(load().sc_check(_stream(torch, device)))
+
+
+def energy(img):
+    """e1 energy of an H x W x C uint8 CUDA image -> H x W uint16 CUDA tensor."""
+    torch = _torch()
+    _check_device_u8(img)
+    H, W, C = _img_shape(img)
+    out = torch.empty((H, W), dtype=torch.uint16, device=img.device)
+    _raise(load().sc_energy(_ptr(img), H, W, C, _ptr(out), _stream(torch, img.device)))
+    return out
+
+
+def find_seam(e):
+    """Algorithm 3 seam of an H x W uint16 CUDA energy map -> (int32[H] seam, int64[1] cost)."""
+    torch = _torch()
+    if e.device.type != "cuda" or e.dtype != torch.uint16 or e.dim() != 2 or not e.is_contiguous():
+        raise ValueError("energy must be a contiguous H x W uint16 CUDA tensor")
+    H, W = e.shape
+    seam = torch.empty(H, dtype=torch.int32, device=e.device)
+    cost = torch.empty(1, dtype=torch.int64, device=e.device)
+    _raise(load().sc_find_seam(_ptr(e), H, W, _ptr(seam), _ptr(cost), _stream(torch, e.device)))
+    return seam, cost
+
+
+def carve(img, target_w: int, target_h: int, with_log: bool = False, plain: bool = False):
+    """Remove (W - target_w) vertical then (H - target_h) horizontal seams on the GPU.
+
+    Returns the target_h x target_w x C uint8 CUDA tensor, or (out, seam_log, cost_log) with
+    ``with_log``. ``plain`` selects the per-seam-launch baseline path (same result)."""
+    torch = _torch()
+    _check_device_u8(img)
+    H, W, C = _img_shape(img)
+    shape = (target_h, target_w) if img.dim() == 2 else (target_h, target_w, C)
+    out = torch.empty(shape, dtype=torch.uint8, device=img.device)
+    log = cost = None
+    if with_log:
+        n = (W - target_w) * H + (H - target_h) * target_w
+        log = torch.empty(max(n, 1), dtype=torch.int32, device=img.device)
+        cost = torch.empty(max(W - target_w + H - target_h, 1), dtype=torch.int64, device=img.device)
+    fn = load().sc_carve_plain if plain else load().sc_carve
+    _raise(fn(_ptr(img), H, W, C, int(target_w), int(target_h), _ptr(out), _ptr(log), _ptr(cost),
+              _stream(torch, img.device)))
+    if with_log:
+        nv, nh = W - target_w, H - target_h
+        return out, log[: nv * H + nh * target_w], cost[: nv + nh]
+    return out
+
+
+def carve_host(img: np.ndarray, target_w: int, target_h: int, stream=None) -> np.ndarray:
+    """sc_carve_host: host image in, host image out (copies inside the call)."""
+    torch = _torch()
+    a = np.ascontiguousarray(img, dtype=np.uint8)
+    if a.ndim == 2:
+        a = a[:, :, None]
+    H, W, C = a.shape
+    out = np.empty((target_h, target_w, C), dtype=np.uint8)
+    st = ctypes.c_void_p(stream) if stream is not None else _stream(torch, None)
+    _raise(load().sc_carve_host(ctypes.c_void_p(a.ctypes.data), H, W, C, int(target_w), int(target_h),
+                                ctypes.c_void_p(out.ctypes.data), st))
+    return out if img.ndim == 3 else out[:, :, 0]
+
+
+def carve_batch(imgs: Sequence, targets: Sequence[Tuple[int, int]], with_log: bool = False):
+    """sc_carve_batch over CUDA images; returns the list of outputs (and seam logs)."""
+    torch = _torch()
+    descs = (ImageDesc * len(imgs))()
+    outs, logs = [], []
+    for k, (img, (tw, th)) in enumerate(zip(imgs, targets)):
+        _check_device_u8(img)
+        H, W, C = _img_shape(img)
+        shape = (th, tw) if img.dim() == 2 else (th, tw, C)
+        out = torch.empty(shape, dtype=torch.uint8, device=img.device)
+        outs.append(out)
+        log = None
+        if with_log:
+            log = torch.empty(max((W - tw) * H + (H - th) * tw, 1), dtype=torch.int32, device=img.device)
+        logs.append(log)
+        descs[k] = ImageDesc(img.data_ptr(), out.data_ptr(), log.data_ptr() if log is not None else 0,
+                             H, W, C, int(tw), int(th), 0)
+    dev = imgs[0].device if len(imgs) else None
+    _raise(load().sc_carve_batch(ctypes.cast(descs, ctypes.c_void_p), len(imgs), _stream(torch, dev)))
+    return (outs, logs) if with_log else outs
+
+
+def timing_enable(on: bool = True) -> None:
+    _raise(load().sc_timing_enable(1 if on else 0))
+
+
+def timing_reset() -> None:
+    _raise(load().sc_timing_reset())
+
+
+def timing_read(kernel: str) -> Tuple[float, int]:
+    """(summed device ms, launches) of one kernel since the last reset; ("all") -> (0, launches)."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _raise(load().sc_timing_read(kernel.encode(), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value

@@ -1,0 +1,77 @@
+// Internal declarations of libsc_gb300 (not part of the C ABI).
+//
+// Device data layout (one image being carved):
+//   img   : uint32 per pixel (channel c in byte c, unused bytes 0), H rows x pitch_img words.
+//           Kept in the current (carved) coordinates.
+//   E     : uint16 energy, H rows x pitch_e elements; column j of row i lives at
+//           E + i*pitch_e + E_PADL + j. The pads keep every window load of the seam search in
+//           bounds; their contents are never used for a result.
+//   Mrow  : uint32 cost-table rows saved at super-tile boundaries (see sc_dp.cu), same padding.
+//   seam  : int32[H]; patch: uint32[H] (the two refreshed energies of a row, low/high half).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sc {
+
+constexpr int E_PADL = 256;    // left pad (elements) of E and Mrow rows
+constexpr int E_PADR = 1024;   // right pad (elements)
+
+// Seam-search geometry (sc_dp.cu). A lane owns V consecutive columns; a warp's window is
+// 32*V columns, of which Q = 32*V - 2*KT are its own strip; windows exchange boundary rows every
+// KT rows inside a CTA (shared memory) and every K2 rows between the CTAs of a cluster (DSMEM).
+// Ancestors are tracked over super-tiles of KS rows.
+constexpr int V = 4;
+constexpr int KT = 16;
+constexpr int Q = 32 * V - 2 * KT;   // 96
+constexpr int KS = 64;
+constexpr int K2 = 64;
+constexpr int MAX_CLUSTER = 16;
+
+// Error bits recorded on the device.
+constexpr int ERR_FILL_MISMATCH = 1;   // backtrack fill disagrees with the ancestor chain
+constexpr int ERR_COST_MISMATCH = 2;   // recomputed cost disagrees with the argmin
+constexpr int ERR_ENERGY_RANGE = 4;    // energies too large for the 24-bit cost field
+constexpr int ERR_TIMEOUT = 8;         // a bounded wait ran out
+constexpr int ERR_BAD_SEAM = 16;       // a seam column out of range
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+inline int pitch_e_for(int W) { return E_PADL + round_up(W, 8) + E_PADR; }
+
+struct DpShape {
+  int nw;    // warps per CTA (4 or 8)
+  int cs;    // CTAs in the cluster
+  int ow;    // CTA-own columns = nw*Q - 2*K2
+};
+DpShape dp_shape_for(int W);
+size_t dp_smem_bytes(int nw, int H);
+
+struct DpArgs {
+  const uint16_t *E;   // row 0, column 0 (already offset by E_PADL)
+  int pitch_e;
+  int H, W;
+  uint32_t *Mrow;      // super-tile boundary rows, row s at Mrow + s*pitch_e (offset by E_PADL)
+  int32_t *seam;       // out [H]
+  int32_t *seam_log;   // nullable, out [H]
+  int64_t *cost;       // nullable, out [1]
+  int *err;            // device error word
+  const int *gate;     // nullable: if *gate != 0 the search is skipped (energy range failure)
+};
+
+// Launchers (enqueue on `st`; return cudaError_t of the launch).
+cudaError_t launch_pack(const uint8_t *src, int H, int W, int C, uint32_t *img, int pitch_img, cudaStream_t st);
+cudaError_t launch_unpack(const uint32_t *img, int pitch_img, int H, int W, int C, bool transposed, uint8_t *dst,
+                          cudaStream_t st);
+cudaError_t launch_transpose(const uint32_t *src, int pitch_src, int H, int W, uint32_t *dst, int pitch_dst,
+                             cudaStream_t st);
+cudaError_t launch_energy(const uint32_t *img, int pitch_img, int H, int W, uint16_t *E, int pitch_e, cudaStream_t st);
+cudaError_t launch_copy_energy(const uint16_t *src, int H, int W, uint16_t *E, int pitch_e, int *err, int *gate,
+                               cudaStream_t st);
+cudaError_t launch_unpad_energy(const uint16_t *E, int pitch_e, int H, int W, uint16_t *dst, cudaStream_t st);
+cudaError_t launch_patch(const uint32_t *img, int pitch_img, int H, int W, const int32_t *seam, uint32_t *patch,
+                         int *err, cudaStream_t st);
+cudaError_t launch_shift(uint32_t *img, int pitch_img, uint16_t *E, int pitch_e, int H, int W, const int32_t *seam,
+                         const uint32_t *patch, cudaStream_t st);
+cudaError_t launch_dp(const DpArgs &a, cudaStream_t st);
+
+}  // namespace sc

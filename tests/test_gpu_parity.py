@@ -1,0 +1,149 @@
+"""Parity of the CUDA path (called through the C ABI) with the oracle: bit-exact energies, seams,
+costs and carved images."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_21207_gb300 import binding as sc
+from paper_2410_21207_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.fail("the -m gpu tests need a CUDA GPU")
+    return torch.device("cuda:0")
+
+
+def _to_dev(a, dev):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+def _np(t):
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("C", [1, 3, 4])
+def test_energy_parity(dev, C):
+    rng = np.random.default_rng(100 + C)
+    shapes = [(1, 1), (1, 7), (7, 1), (2, 2), (3, 17), (16, 16), (17, 33), (31, 129), (64, 257), (300, 1001)]
+    for H, W in shapes:
+        img = rng.integers(0, 256, size=(H, W, C)).astype(np.uint8)
+        got = _np(sc.energy(_to_dev(img, dev)))
+        np.testing.assert_array_equal(got, oracle.energy(img), err_msg=f"{H}x{W}x{C}")
+    sc.check()
+
+
+def _energies(rng, H, W):
+    yield "uniform", rng.integers(0, 1531, size=(H, W))
+    yield "ties", rng.integers(0, 3, size=(H, W))
+    yield "constant", np.full((H, W), 7)
+    yield "stripes", np.tile(rng.integers(0, 50, size=(1, W)), (H, 1))
+
+
+SEAM_SHAPES = [
+    (1, 1), (1, 2), (2, 1), (1, 300), (5, 3), (16, 17), (17, 96), (63, 97), (64, 255), (65, 256), (127, 257),
+    (128, 513), (129, 1000), (200, 1920), (300, 2049), (70, 3000), (40, 4096), (40, 4097), (33, 6000),
+    (20, 8192), (1080, 64), (8192, 40),
+]
+
+
+@pytest.mark.parametrize("H,W", SEAM_SHAPES)
+def test_find_seam_parity(dev, H, W):
+    rng = np.random.default_rng(H * 10007 + W)
+    for kind, e in _energies(rng, H, W):
+        e = e.astype(np.uint16)
+        seam, cost = sc.find_seam(_to_dev(e, dev))
+        sc.check()
+        s_ref, c_ref = oracle.dp_seam(e)
+        assert int(_np(cost)[0]) == c_ref, (H, W, kind)
+        np.testing.assert_array_equal(_np(seam), s_ref, err_msg=f"{H}x{W} {kind}")
+
+
+def test_find_seam_energy_range_rejected(dev):
+    e = np.full((2000, 16), 60000, dtype=np.uint16)   # 2000 * 60000 >= 2^24
+    sc.find_seam(_to_dev(e, dev))
+    with pytest.raises(sc.ScError) as ei:
+        sc.check()
+    assert ei.value.code == sc.SC_EINVAL
+    sc.check()   # cleared
+
+
+def _carve_ref(img, tw, th):
+    return oracle.carve(img, tw, th, with_log=True)
+
+
+def _carve_cmp(dev, img, tw, th, plain=False):
+    out, log, cost = sc.carve(_to_dev(img, dev), tw, th, with_log=True, plain=plain)
+    sc.check()
+    r_out, r_log, r_cost = _carve_ref(img, tw, th)
+    np.testing.assert_array_equal(_np(log), r_log)
+    np.testing.assert_array_equal(_np(cost), r_cost)
+    np.testing.assert_array_equal(_np(out), r_out)
+
+
+def test_carve_small_both_passes(dev):
+    rng = np.random.default_rng(31)
+    for k in range(25):
+        H, W = int(rng.integers(1, 90)), int(rng.integers(1, 140))
+        C = int(rng.choice([1, 3, 4]))
+        tw, th = int(rng.integers(1, W + 1)), int(rng.integers(1, H + 1))
+        if k % 3 == 0:
+            img = rng.integers(0, 4, size=(H, W, C)).astype(np.uint8)   # many exact ties
+        else:
+            img = rng.integers(0, 256, size=(H, W, C)).astype(np.uint8)
+        _carve_cmp(dev, img, tw, th, plain=(k % 2 == 0))
+
+
+def test_carve_config1(dev):
+    job = synth.config1()
+    _carve_cmp(dev, job.make(), job.target_w, job.target_h)
+
+
+def test_carve_generated_multi_cta(dev):
+    """A generated image wide enough for a multi-CTA cluster and tall enough for several
+    super-tiles, with a ragged last tile; both passes."""
+    img = synth.gen_image(700, 333, 12, 20, 200, 91)
+    _carve_cmp(dev, img, 650, 300)
+
+
+def test_carve_config2_full(dev):
+    """1920x1080 -> 1440 (480 vertical seams): every seam index and every output byte."""
+    job = synth.config2()
+    _carve_cmp(dev, job.make(), job.target_w, job.target_h)
+
+
+def test_plain_and_fast_paths_agree(dev):
+    img = synth.gen_image(400, 260, 8, 20, 120, 5)
+    a = _np(sc.carve(_to_dev(img, dev), 330, 220))
+    b = _np(sc.carve(_to_dev(img, dev), 330, 220, plain=True))
+    np.testing.assert_array_equal(a, b)
+
+
+def test_carve_host_entry_point(dev):
+    img = synth.gen_image(300, 200, 6, 20, 100, 17)
+    out = sc.carve_host(img, 250, 180)
+    np.testing.assert_array_equal(out, oracle.carve(img, 250, 180))
+
+
+def test_batch_equals_alone(dev):
+    jobs = synth.config4(n=6, seed=44)
+    imgs = [j.make() for j in jobs]
+    d = [_to_dev(i, dev) for i in imgs]
+    outs, logs = sc.carve_batch(d, [(j.target_w, j.target_h) for j in jobs], with_log=True)
+    sc.check()
+    for img, j, o, lg in zip(imgs, jobs, outs, logs):
+        r_out, r_log, _ = _carve_ref(img, j.target_w, j.target_h)
+        np.testing.assert_array_equal(_np(o), r_out)
+        np.testing.assert_array_equal(_np(lg)[: len(r_log)], r_log)
+
+
+def test_invalid_arguments_raise(dev):
+    img = _to_dev(np.zeros((10, 10, 3), dtype=np.uint8), dev)
+    with pytest.raises(sc.ScError):
+        sc.carve(img, 11, 10)
+    with pytest.raises(sc.ScError):
+        sc.carve(img, 0, 10)
