@@ -96,6 +96,26 @@ int sc_energy(const uint8_t *img, int H, int W, int C, uint16_t *energy_out, voi
  *         or energies that could overflow (checked on the device: SC_EINTERNAL via sc_check). */
 int sc_find_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_t *cost_out, void *stream);
 
+/* ---- sc_find_seam without allocation (the paper has no counterpart: this is a deployment aid) ----
+ * For programs that must not let a library allocate device memory: cudaMalloc/cudaFree can
+ * synchronise the device and take unpredictable time inside a latency-critical loop, and hosts
+ * that budget every device byte through their own allocator forbid allocations they do not
+ * control. Same arguments, result and limits as sc_find_seam, but every scratch byte (a padded
+ * copy of the energy map, the saved cost rows, two status words) lives in one fixed array of
+ * 32 MiB inside the library's device image, held by every GPU that loads the library until the
+ * process exits; the call never calls cudaMalloc or cudaFree.
+ *   - Size limit: the map must fit the array, roughly H * (W + 1280) * 2 bytes plus one row of
+ *     4-byte costs per 64 rows (3840 x 2160 fits). Larger maps return SC_EINVAL (a message naming
+ *     the bytes needed goes to stderr), before any work is enqueued.
+ *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress);
+ *     make that first call before any stream capture.
+ *   - All calls share the one array, which keeps the previous call's contents: calls whose work
+ *     overlaps on the GPU (different streams, or different host threads) race and must be
+ *     serialised by the caller. The status words are cleared by each call.
+ *   - If H * max(energy) could reach 2^24, the search is skipped and every entry of seam_out (and
+ *     *cost_out when given) is set to -1. Argument errors: as sc_find_seam. */
+int sc_find_seam_static(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_t *cost_out, void *stream);
+
 /* ---- carve: remove (W - target_w) vertical seams, then (H - target_h) horizontal seams (found
  * as vertical seams of the transposed image), recomputing the energy where the removal changed
  * it (sections "Removal of Seams" and "Design Techniques"). The result equals: for each seam,

@@ -61,6 +61,7 @@ def load(path: Optional[str] = None):
                 "sc_release_workspaces": ([], I),
                 "sc_energy": ([P, I, I, I, P, P], I),
                 "sc_find_seam": ([P, I, I, P, P, P], I),
+                "sc_find_seam_static": ([P, I, I, P, P, P], I),
                 "sc_carve": ([P, I, I, I, I, I, P, P, P, P], I),
                 "sc_carve_plain": ([P, I, I, I, I, I, P, P, P, P], I),
                 "sc_carve_host": ([P, I, I, I, I, I, P, P], I),
@@ -139,6 +140,21 @@ def find_seam(e):
     seam = torch.empty(H, dtype=torch.int32, device=e.device)
     cost = torch.empty(1, dtype=torch.int64, device=e.device)
     _raise(load().sc_find_seam(_ptr(e), H, W, _ptr(seam), _ptr(cost), _stream(torch, e.device)))
+    return seam, cost
+
+
+def find_seam_static(e):
+    """sc_find_seam_static: the same search as find_seam, with the library's fixed scratch array
+    instead of allocated scratch (for callers that must not allocate device memory)."""
+    torch = _torch()
+    if e.device.type != "cuda" or e.dtype != torch.uint16 or e.dim() != 2 or not e.is_contiguous():
+        raise ValueError("energy must be a contiguous H x W uint16 CUDA tensor")
+    H, W = e.shape
+    seam = torch.empty(H, dtype=torch.int32, device=e.device)
+    cost = torch.empty(1, dtype=torch.int64, device=e.device)
+    code = load().sc_find_seam_static(_ptr(e), H, W, _ptr(seam), _ptr(cost), _stream(torch, e.device))
+    if code != SC_OK:
+        raise ScError(code, "sc_find_seam_static rejected its arguments")
     return seam, cost
 
 
