@@ -157,9 +157,27 @@ typedef struct {
   int reserved;
 } sc_image_desc;
 
-/* descs: HOST array of n descriptors (copied during the call). Errors: SC_EINVAL if n < 1,
- * descs is NULL or any descriptor fails the sc_carve checks (nothing is enqueued then). */
+/* descs: HOST array of n descriptors (copied during the call). One persistent launch: each CTA
+ * takes the next image from a queue and carves it completely (energy, every seam's search,
+ * refresh and compaction, the transposed horizontal pass). Images whose searched width exceeds
+ * what one CTA covers (1440 columns in the default configuration) are carved by the cluster path
+ * of sc_carve on the same stream. The call waits for the previous batch on `stream` before reusing
+ * its scratch. Errors: SC_EINVAL if n < 1, descs is NULL or any descriptor fails the sc_carve
+ * checks (nothing is enqueued then); device-side errors via sc_check. */
 int sc_carve_batch(const sc_image_desc *descs, int n, void *stream);
+
+/* A batch plan: the scratch, the descriptor table and a CUDA graph of the persistent launch,
+ * built once and replayed. autotune != 0 times every tile height / warp-count configuration
+ * (DP tile height 8, 16 or 32 rows; 8 or 15 compute warps per CTA) on the real batch and keeps
+ * the fastest. The images' contents may change between runs; their pointers and sizes may not.
+ * sc_batch_plan_run enqueues one replay on `stream`; sc_batch_plan_info reports the chosen
+ * configuration (compute warps, tile height, CTAs launched, images batched / sent to the
+ * cluster path). */
+typedef struct sc_batch_plan sc_batch_plan;
+int sc_batch_plan_create(const sc_image_desc *descs, int n, int autotune, void *stream, sc_batch_plan **plan);
+int sc_batch_plan_run(sc_batch_plan *plan, void *stream);
+int sc_batch_plan_info(const sc_batch_plan *plan, int *nw, int *kt, int *grid, int *batched, int *fallback);
+int sc_batch_plan_destroy(sc_batch_plan *plan);
 
 #ifdef __cplusplus
 }

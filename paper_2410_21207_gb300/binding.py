@@ -66,6 +66,10 @@ def load(path: Optional[str] = None):
                 "sc_carve_plain": ([P, I, I, I, I, I, P, P, P, P], I),
                 "sc_carve_host": ([P, I, I, I, I, I, P, P], I),
                 "sc_carve_batch": ([P, I, P], I),
+                "sc_batch_plan_create": ([P, I, I, P, P], I),
+                "sc_batch_plan_run": ([P, P], I),
+                "sc_batch_plan_info": ([P, P, P, P, P, P], I),
+                "sc_batch_plan_destroy": ([P], I),
                 "sc_timing_enable": ([I], I),
                 "sc_timing_reset": ([], I),
                 "sc_timing_read": ([ctypes.c_char_p, P, P], I),
@@ -196,8 +200,7 @@ def carve_host(img: np.ndarray, target_w: int, target_h: int, stream=None) -> np
     return out if img.ndim == 3 else out[:, :, 0]
 
 
-def carve_batch(imgs: Sequence, targets: Sequence[Tuple[int, int]], with_log: bool = False):
-    """sc_carve_batch over CUDA images; returns the list of outputs (and seam logs)."""
+def _batch_descs(imgs, targets, with_log):
     torch = _torch()
     descs = (ImageDesc * len(imgs))()
     outs, logs = [], []
@@ -213,9 +216,54 @@ def carve_batch(imgs: Sequence, targets: Sequence[Tuple[int, int]], with_log: bo
         logs.append(log)
         descs[k] = ImageDesc(img.data_ptr(), out.data_ptr(), log.data_ptr() if log is not None else 0,
                              H, W, C, int(tw), int(th), 0)
+    return descs, outs, logs
+
+
+def carve_batch(imgs: Sequence, targets: Sequence[Tuple[int, int]], with_log: bool = False):
+    """sc_carve_batch over CUDA images (one persistent launch); returns the outputs (and seam logs)."""
+    torch = _torch()
+    descs, outs, logs = _batch_descs(imgs, targets, with_log)
     dev = imgs[0].device if len(imgs) else None
     _raise(load().sc_carve_batch(ctypes.cast(descs, ctypes.c_void_p), len(imgs), _stream(torch, dev)))
     return (outs, logs) if with_log else outs
+
+
+class BatchPlan:
+    """sc_batch_plan: scratch, descriptor table and a CUDA graph of the persistent launch, built once
+    (optionally autotuned) and replayed by run(). The input tensors must stay alive and keep their
+    storage; their contents may change between runs."""
+
+    def __init__(self, imgs: Sequence, targets: Sequence[Tuple[int, int]], autotune: bool = False,
+                 with_log: bool = False):
+        torch = _torch()
+        self.imgs = list(imgs)
+        self.descs, self.outs, self.logs = _batch_descs(self.imgs, targets, with_log)
+        self.device = self.imgs[0].device
+        h = ctypes.c_void_p(0)
+        _raise(load().sc_batch_plan_create(ctypes.cast(self.descs, ctypes.c_void_p), len(self.imgs),
+                                           1 if autotune else 0, _stream(torch, self.device), ctypes.byref(h)))
+        self._h = h
+
+    def run(self):
+        torch = _torch()
+        _raise(load().sc_batch_plan_run(self._h, _stream(torch, self.device)))
+        return self.outs
+
+    def info(self) -> dict:
+        v = [ctypes.c_int(0) for _ in range(5)]
+        _raise(load().sc_batch_plan_info(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("compute_warps", "tile_rows", "ctas", "batched", "cluster_path"), (x.value for x in v)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sc_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def timing_enable(on: bool = True) -> None:

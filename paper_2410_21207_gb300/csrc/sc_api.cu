@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/sc.h"
+#include "sc_batch_item.h"
 #include "sc_internal.cuh"
 
 namespace sc {
@@ -69,6 +70,10 @@ template <typename T>
 struct DevBuf {
   T *p = nullptr;
   size_t cap = 0;   // elements
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { release(); }
   cudaError_t ensure(size_t n) {
     if (n <= cap) return cudaSuccess;
     if (p) {
@@ -106,6 +111,22 @@ struct Workspace {
 
 static std::mutex g_ws_mu;
 static std::map<std::pair<int, void *>, Workspace *> g_ws;
+
+// One error word per device for batched launches (plans may run on any stream); sc_check reads it.
+static std::mutex g_gerr_mu;
+static std::map<int, int *> g_gerr;
+static int *device_error_word() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_gerr_mu);
+  auto it = g_gerr.find(dev);
+  if (it != g_gerr.end()) return it->second;
+  int *p = nullptr;
+  if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+  if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+  g_gerr[dev] = p;
+  return p;
+}
 
 static int get_ws(void *stream, Workspace **out) {
   int dev = 0;
@@ -235,11 +256,17 @@ int sc_check(void *stream) {
   Workspace &ws = *wsp;
   std::lock_guard<std::mutex> lk(ws.mu);
   SC_CUDA(cudaStreamSynchronize(st));
-  if (!ws.flags.p) return SC_OK;
+  SC_CUDA(ws.flags.ensure(4));
   int h[2] = {0, 0};
   SC_CUDA(cudaMemcpy(h, ws.flags.p, 2 * sizeof(int), cudaMemcpyDeviceToHost));
   SC_CUDA(cudaMemset(ws.flags.p, 0, 2 * sizeof(int)));
-  const int e = h[0];
+  int e = h[0];
+  if (int *ge = device_error_word()) {
+    int g = 0;
+    SC_CUDA(cudaMemcpy(&g, ge, sizeof(int), cudaMemcpyDeviceToHost));
+    if (g) SC_CUDA(cudaMemset(ge, 0, sizeof(int)));
+    e |= g;
+  }
   if (e & ERR_TIMEOUT) return fail(SC_ETIMEOUT, "a bounded device wait ran out (error word 0x%x)", e);
   if (e & ERR_ENERGY_RANGE) return fail(SC_EINVAL, "energies too large: a seam sum could reach 2^24");
   if (e) return fail(SC_EINTERNAL, "device consistency check failed (error word 0x%x)", e);
@@ -372,19 +399,270 @@ int sc_carve_host(const uint8_t *img_host, int H, int W, int C, int target_w, in
   return sc_check(stream);
 }
 
-int sc_carve_batch(const sc_image_desc *descs, int n, void *stream) {
+}  // extern "C"
+
+namespace sc {
+
+// ---- batched carve (one persistent launch; images wider than a CTA go to the cluster path) ----
+struct BatchCfg {
+  int nw, kt;
+};
+static const BatchCfg kBatchCfgs[] = {{15, 16}, {15, 8}, {8, 16}, {8, 8}, {8, 32}};
+
+static int batch_need_width(const sc_image_desc &d) {
+  const int nh = d.H - d.target_h;
+  return nh > 0 ? (d.W > d.H ? d.W : d.H) : d.W;
+}
+
+struct BatchSetup {
+  std::vector<BatchItem> items;   // batched images (device pointers filled in)
+  std::vector<int> fallback;      // descriptor indices carved by the cluster path
+  size_t pool_bytes = 0;
+  int Smax = 1;
+};
+
+static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Lays out every batched image's scratch in one pool (offsets; `pool` may be null to size it).
+static void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned char *pool, BatchSetup &b) {
+  b.items.clear();
+  b.fallback.clear();
+  b.Smax = 1;
+  size_t off = 0;
+  const int limit = batch_width_limit(c.nw, c.kt);
+  for (int k = 0; k < n; ++k) {
+    const sc_image_desc &d = descs[k];
+    if (batch_need_width(d) > limit) {
+      b.fallback.push_back(k);
+      continue;
+    }
+    const int nh = d.H - d.target_h;
+    const int R = d.H > d.W ? d.H : d.W;
+    const int rows_max = (nh > 0 && d.target_w > d.H) ? d.target_w : d.H;
+    const int cols_max = nh > 0 ? R : d.W;
+    BatchItem it;
+    it.img = d.img;
+    it.out = d.out;
+    it.seam_log = d.seam_log;
+    it.cost_log = nullptr;
+    it.H = d.H; it.W = d.W; it.C = d.C; it.tw = d.target_w; it.th = d.target_h;
+    it.pitch = round_up(R, 4);
+    // the single-CTA search stages columns [-KT, limit + KT) whatever the image width
+    it.pe = pitch_e_for(cols_max > limit + 64 ? cols_max : limit + 64);
+    it.pad = 0;
+    const int S = (rows_max + KS - 1) / KS;
+    if (S > b.Smax) b.Smax = S;
+    auto take = [&](size_t bytes) { unsigned char *p = pool ? pool + off : nullptr; off += a256(bytes); return p; };
+    it.img_w = (uint32_t *)take((size_t)d.H * it.pitch * 4);
+    it.img2_w = nh > 0 ? (uint32_t *)take((size_t)d.target_w * it.pitch * 4) : nullptr;
+    it.E = (uint16_t *)take((size_t)rows_max * it.pe * 2);
+    it.Mrow = (uint32_t *)take((size_t)(S + 1) * it.pe * 4);
+    it.seam = (int32_t *)take((size_t)rows_max * 4);
+    it.patch = (uint32_t *)take((size_t)rows_max * 4);
+    b.items.push_back(it);
+  }
+  b.pool_bytes = off;
+}
+
+static int check_batch_descs(const sc_image_desc *descs, int n) {
   if (!descs || n < 1) return fail(SC_EINVAL, "empty batch");
   for (int k = 0; k < n; ++k) {
     const sc_image_desc &d = descs[k];
     int rc = check_carve_args(d.img, d.H, d.W, d.C, d.target_w, d.target_h, d.out);
     if (rc) return fail(rc, "descriptor %d: %s", k, g_last_error.c_str());
   }
-  for (int k = 0; k < n; ++k) {
+  return SC_OK;
+}
+
+// the widest configuration whose shared memory fits this batch and that covers the most images
+static BatchCfg default_batch_cfg(const sc_image_desc *descs, int n) {
+  BatchCfg best = kBatchCfgs[0];
+  int best_cover = -1;
+  for (const BatchCfg &c : kBatchCfgs) {
+    BatchSetup b;
+    batch_layout(descs, n, c, nullptr, b);
+    if (batch_smem_bytes(c.nw, c.kt, b.Smax) > 232448 - 64) continue;
+    const int cover = (int)b.items.size();
+    if (cover > best_cover) { best_cover = cover; best = c; }
+  }
+  return best;
+}
+
+struct BatchRun {
+  DevBuf<unsigned char> pool;
+  DevBuf<BatchItem> items;
+  DevBuf<int> queue;
+  BatchSetup setup;
+  BatchCfg cfg{15, 16};
+  int grid = 1;
+};
+
+// Allocates and uploads everything one batched launch needs (synchronous upload).
+static int batch_prepare(BatchRun &r, const sc_image_desc *descs, int n, const BatchCfg &c) {
+  r.cfg = c;
+  batch_layout(descs, n, c, nullptr, r.setup);
+  SC_CUDA(r.pool.ensure(r.setup.pool_bytes ? r.setup.pool_bytes : 256));
+  batch_layout(descs, n, c, r.pool.p, r.setup);
+  const int nb = (int)r.setup.items.size();
+  SC_CUDA(r.items.ensure(nb ? nb : 1));
+  SC_CUDA(r.queue.ensure(1));
+  if (nb) SC_CUDA(cudaMemcpy(r.items.p, r.setup.items.data(), nb * sizeof(BatchItem), cudaMemcpyHostToDevice));
+  int dev = 0, sms = 1;
+  SC_CUDA(cudaGetDevice(&dev));
+  SC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int per_sm = batch_blocks_per_sm(c.nw, c.kt, r.setup.Smax);
+  r.grid = sms * per_sm;
+  if (r.grid > nb) r.grid = nb;
+  if (r.grid < 1) r.grid = 1;
+  return SC_OK;
+}
+
+static int batch_enqueue(BatchRun &r, const sc_image_desc *descs, cudaStream_t st, int *err) {
+  const int nb = (int)r.setup.items.size();
+  if (nb) {
+    SC_CUDA(cudaMemsetAsync(r.queue.p, 0, sizeof(int), st));
+    SC_CUDA(timed("carve_batch", st, [&] {
+      return launch_batch(r.cfg.nw, r.cfg.kt, r.items.p, nb, r.setup.Smax, r.grid, r.queue.p, err, st);
+    }));
+  }
+  for (int k : r.setup.fallback) {
     const sc_image_desc &d = descs[k];
-    int rc = carve_impl(d.img, d.H, d.W, d.C, d.target_w, d.target_h, d.out, d.seam_log, nullptr,
-                        (cudaStream_t)stream);
+    int rc = carve_impl(d.img, d.H, d.W, d.C, d.target_w, d.target_h, d.out, d.seam_log, nullptr, st);
     if (rc) return rc;
   }
+  return SC_OK;
+}
+
+}  // namespace sc
+
+struct sc_batch_plan {
+  sc::BatchRun run;
+  std::vector<sc_image_desc> descs;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int *err = nullptr;
+};
+
+extern "C" {
+
+int sc_carve_batch(const sc_image_desc *descs, int n, void *stream) {
+  int rc = check_batch_descs(descs, n);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  int *err = device_error_word();
+  if (!err) return fail(SC_ECUDA, "cannot allocate the device error word");
+  static std::mutex mu;
+  static std::map<std::pair<int, void *>, BatchRun *> runs;   // scratch reused per (device, stream)
+  int dev = 0;
+  SC_CUDA(cudaGetDevice(&dev));
+  BatchRun *r;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto key = std::make_pair(dev, stream);
+    auto it = runs.find(key);
+    if (it == runs.end()) it = runs.emplace(key, new BatchRun()).first;
+    r = it->second;
+  }
+  SC_CUDA(cudaStreamSynchronize(st));   // the previous batch on this stream may still use the scratch
+  if ((rc = batch_prepare(*r, descs, n, default_batch_cfg(descs, n)))) return rc;
+  return batch_enqueue(*r, descs, st, err);
+}
+
+int sc_batch_plan_create(const sc_image_desc *descs, int n, int autotune, void *stream, sc_batch_plan **out) {
+  if (!out) return fail(SC_EINVAL, "null plan pointer");
+  *out = nullptr;
+  int rc = check_batch_descs(descs, n);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  sc_batch_plan *p = new sc_batch_plan();
+  p->descs.assign(descs, descs + n);
+  p->err = device_error_word();
+  if (!p->err) { delete p; return fail(SC_ECUDA, "cannot allocate the device error word"); }
+  BatchCfg best = default_batch_cfg(descs, n);
+  if (autotune) {
+    // time every configuration that batches as many images as the default, on the real batch
+    BatchSetup b0;
+    batch_layout(descs, n, best, nullptr, b0);
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    SC_CUDA(cudaEventCreate(&e0));
+    SC_CUDA(cudaEventCreate(&e1));
+    for (const BatchCfg &c : kBatchCfgs) {
+      BatchSetup b;
+      batch_layout(descs, n, c, nullptr, b);
+      if (b.items.size() < b0.items.size()) continue;
+      if (batch_smem_bytes(c.nw, c.kt, b.Smax) > 232448 - 64) continue;
+      BatchRun trial;
+      if ((rc = batch_prepare(trial, descs, n, c))) { delete p; return rc; }
+      BatchSetup keep = trial.setup;
+      trial.setup.fallback.clear();   // time the batched launch alone
+      if ((rc = batch_enqueue(trial, descs, st, p->err))) { delete p; return rc; }
+      SC_CUDA(cudaEventRecord(e0, st));
+      if ((rc = batch_enqueue(trial, descs, st, p->err))) { delete p; return rc; }
+      SC_CUDA(cudaEventRecord(e1, st));
+      SC_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      SC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) { best_ms = ms; best = c; }
+      trial.setup = keep;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  if ((rc = batch_prepare(p->run, descs, n, best))) { delete p; return rc; }
+  // capture the batched launch (queue reset + persistent kernel) in a CUDA graph
+  const int nb = (int)p->run.setup.items.size();
+  if (nb) {
+    cudaStream_t cap;
+    SC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    SC_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = cudaMemsetAsync(p->run.queue.p, 0, sizeof(int), cap);
+    cudaError_t e2 = launch_batch(best.nw, best.kt, p->run.items.p, nb, p->run.setup.Smax, p->run.grid,
+                                  p->run.queue.p, p->err, cap);
+    cudaError_t e3 = cudaStreamEndCapture(cap, &p->graph);
+    cudaStreamDestroy(cap);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+      delete p;
+      return fail(SC_ECUDA, "graph capture failed: %s / %s / %s", cudaGetErrorString(e1), cudaGetErrorString(e2),
+                  cudaGetErrorString(e3));
+    }
+    SC_CUDA(cudaGraphInstantiate(&p->exec, p->graph, 0));
+  }
+  *out = p;
+  return SC_OK;
+}
+
+int sc_batch_plan_run(sc_batch_plan *plan, void *stream) {
+  if (!plan) return fail(SC_EINVAL, "null plan");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (plan->exec) SC_CUDA(timed("carve_batch", st, [&] { return cudaGraphLaunch(plan->exec, st); }));
+  for (int k : plan->run.setup.fallback) {
+    const sc_image_desc &d = plan->descs[k];
+    int rc = carve_impl(d.img, d.H, d.W, d.C, d.target_w, d.target_h, d.out, d.seam_log, nullptr, st);
+    if (rc) return rc;
+  }
+  return SC_OK;
+}
+
+int sc_batch_plan_info(const sc_batch_plan *plan, int *nw, int *kt, int *grid, int *batched, int *fallback) {
+  if (!plan) return fail(SC_EINVAL, "null plan");
+  if (nw) *nw = plan->run.cfg.nw;
+  if (kt) *kt = plan->run.cfg.kt;
+  if (grid) *grid = plan->run.grid;
+  if (batched) *batched = (int)plan->run.setup.items.size();
+  if (fallback) *fallback = (int)plan->run.setup.fallback.size();
+  return SC_OK;
+}
+
+int sc_batch_plan_destroy(sc_batch_plan *plan) {
+  if (!plan) return SC_OK;
+  cudaDeviceSynchronize();
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  plan->run.pool.release();
+  plan->run.items.release();
+  plan->run.queue.release();
+  delete plan;
   return SC_OK;
 }
 

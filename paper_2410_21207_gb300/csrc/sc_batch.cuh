@@ -1,0 +1,159 @@
+// Batched persistent carving: one launch carves many images of uneven sizes. Each CTA repeatedly
+// takes the next image from a queue (one atomic counter) and carves it completely on its own: pack,
+// e1 energy, every vertical seam (search, local refresh, compaction), the horizontal pass through a
+// transposition, and unpack, with CTA barriers between the phases. The seam search is
+// seam_search<NW, KT, false> (sc_search.cuh), so an image fits one CTA when every searched width
+// is at most NW * (32*V - 2*KT) columns; the host routes wider images to the cluster path.
+#pragma once
+#include "sc_batch_item.h"
+#include "sc_rowops.cuh"
+#include "sc_search.cuh"
+
+namespace sc {
+
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// rows x cols word image -> its transpose (cols x rows), 32x32 tiles staged in shared memory; `tile`
+// holds `ntw` warps' 32x33 tiles.
+__device__ inline void cta_transpose(const uint32_t *src, int ps, int rows, int cols, uint32_t *dst, int pd,
+                                     uint32_t *tile, int ntw) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp >= ntw) return;
+  uint32_t *t = tile + warp * 32 * 33;
+  const int tr = (rows + 31) / 32, tc = (cols + 31) / 32;
+  for (int tix = warp; tix < tr * tc; tix += ntw) {
+    const int by = (tix / tc) * 32, bx = (tix % tc) * 32;
+    for (int r = 0; r < 32; ++r) {
+      const int i = by + r, j = bx + lane;
+      if (i < rows && j < cols) t[r * 33 + lane] = src[(int64_t)i * ps + j];
+    }
+    __syncwarp();
+    for (int r = 0; r < 32; ++r) {
+      const int j = bx + r, i = by + lane;   // dst row j, column i
+      if (i < rows && j < cols) dst[(int64_t)j * pd + i] = t[lane * 33 + r];
+    }
+    __syncwarp();
+  }
+}
+
+template <int NW, int KT>
+__device__ void batch_seam_pass(const BatchItem &it, uint32_t *words, int rows, int cols, int count,
+                                int32_t *log, int64_t *costs, unsigned char *smem, int Smax, SearchState &st,
+                                int *err) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+  for (int t = 0; t < count; ++t) {
+    const int w = cols - t;
+    SearchArgs a;
+    a.E = it.E + E_PADL;
+    a.pitch_e = it.pe;
+    a.H = rows;
+    a.W = w;
+    a.Mrow = it.Mrow + E_PADL;
+    a.seam = it.seam;
+    a.seam_log = log ? log + (size_t)t * rows : nullptr;
+    a.cost = costs ? costs + t : nullptr;
+    a.err = err;
+    a.gated = false;
+    seam_search<NW, KT, false>(a, smem, Smax, st);   // ends with a CTA barrier: seam[] is complete
+    bool bad = false;
+    for (int i = tid; i < rows; i += nthr) it.patch[i] = patch_row(words, it.pitch, rows, w, it.seam, i, &bad);
+    if (bad) atomicOr(err, ERR_BAD_SEAM);
+    __syncthreads();
+    for (int i = warp; i < rows; i += nwarps) {
+      const int s = it.seam[i];
+      if (s >= 0 && s < w) compact_row(words, it.pitch, it.E + E_PADL, it.pe, w, s, it.patch[i], i, lane);
+    }
+    fence_proxy_async_global();   // the next search stages the energy rows with TMA (async proxy)
+    __syncthreads();
+  }
+}
+
+template <int NW, int KT>
+__device__ void batch_energy(const uint32_t *words, int pitch, int rows, int cols, uint16_t *E, int pe) {
+  const int64_t n = (int64_t)rows * cols;
+  for (int64_t q = threadIdx.x; q < n; q += blockDim.x) {
+    const int i = (int)(q / cols), j = (int)(q % cols);
+    E[(int64_t)i * pe + j] = (uint16_t)energy_at(words, pitch, rows, cols, i, j);
+  }
+  fence_proxy_async_global();
+  __syncthreads();
+}
+
+template <int NW, int KT>
+__device__ void batch_carve_item(const BatchItem &it, unsigned char *smem, int Smax, SearchState &st, int *err) {
+  const int H = it.H, W = it.W, C = it.C, tw = it.tw, th = it.th;
+  const int64_t npx = (int64_t)H * W;
+  for (int64_t q = threadIdx.x; q < npx; q += blockDim.x) {
+    const int i = (int)(q / W), j = (int)(q % W);
+    it.img_w[(int64_t)i * it.pitch + j] = pack_pixel(it.img + q * C, C);
+  }
+  __syncthreads();
+  batch_energy<NW, KT>(it.img_w, it.pitch, H, W, it.E + E_PADL, it.pe);
+  const int nv = W - tw, nh = H - th;
+  batch_seam_pass<NW, KT>(it, it.img_w, H, W, nv, it.seam_log, it.cost_log, smem, Smax, st, err);
+  uint32_t *res = it.img_w;
+  if (nh > 0) {
+    const SearchPlan plan = search_plan<NW, KT, false>(Smax);
+    uint32_t *tile = reinterpret_cast<uint32_t *>(smem + plan.ring);   // the ring is idle between searches
+    const int ntw_fit = (int)((plan.bars - plan.ring) / (32 * 33 * 4));
+    const int ntw = ntw_fit < NW + 1 ? ntw_fit : NW + 1;
+    cta_transpose(it.img_w, it.pitch, H, tw, it.img2_w, it.pitch, tile, ntw);   // tw rows x H columns
+    __syncthreads();
+    batch_energy<NW, KT>(it.img2_w, it.pitch, tw, H, it.E + E_PADL, it.pe);
+    batch_seam_pass<NW, KT>(it, it.img2_w, tw, H, nh, it.seam_log ? it.seam_log + (size_t)nv * H : nullptr,
+                            it.cost_log ? it.cost_log + nv : nullptr, smem, Smax, st, err);
+    cta_transpose(it.img2_w, it.pitch, tw, th, it.img_w, it.pitch, tile, ntw);  // th rows x tw columns
+    __syncthreads();
+  }
+  const int64_t nout = (int64_t)th * tw;
+  for (int64_t q = threadIdx.x; q < nout; q += blockDim.x) {
+    const int i = (int)(q / tw), j = (int)(q % tw);
+    unpack_pixel(res[(int64_t)i * it.pitch + j], it.out + q * C, C);
+  }
+  __syncthreads();
+}
+
+template <int NW, int KT>
+__global__ void __launch_bounds__(Geo<NW, KT, false>::THREADS, 1)
+    k_batch(const BatchItem *__restrict__ items, int n, int Smax, int *queue, int *err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int next;
+  search_init<NW, KT, false>(smem, Smax);
+  __syncthreads();
+  SearchState st;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(queue, 1);
+    __syncthreads();
+    const int k = next;
+    __syncthreads();
+    if (k >= n) break;
+    batch_carve_item<NW, KT>(items[k], smem, Smax, st, err);
+  }
+}
+
+constexpr size_t BATCH_SMEM_MAX = 232448 - 64;   // the opt-in limit minus the kernel's static shared memory
+
+template <int NW, int KT>
+cudaError_t batch_configure_cfg() {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_batch<NW, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BATCH_SMEM_MAX);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  return cudaSuccess;
+}
+
+template <int NW, int KT>
+cudaError_t launch_batch_cfg(const BatchItem *items, int n, int Smax, int grid, int *queue, int *err,
+                             cudaStream_t st) {
+  const size_t smem = search_plan<NW, KT, false>(Smax).total;
+  if (smem > BATCH_SMEM_MAX) return cudaErrorInvalidValue;
+  cudaError_t e = batch_configure_cfg<NW, KT>();
+  if (e != cudaSuccess) return e;
+  k_batch<NW, KT><<<grid, Geo<NW, KT, false>::THREADS, smem, st>>>(items, n, Smax, queue, err);
+  return cudaGetLastError();
+}
+
+}  // namespace sc

@@ -1,0 +1,33 @@
+// One image of a batched carve, as the persistent kernel reads it (device pointers).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sc {
+
+struct BatchItem {
+  const uint8_t *img;   // H x W x C uint8 (caller's)
+  uint8_t *out;         // th x tw x C uint8 (caller's)
+  int32_t *seam_log;    // nullable (caller's)
+  int64_t *cost_log;    // nullable
+  int H, W, C, tw, th;
+  int pitch;            // words per row of img_w / img2_w (>= max(H, W))
+  int pe;               // energy pitch (elements)
+  int pad;
+  uint32_t *img_w;      // max(H,W) x pitch words: the image being carved
+  uint32_t *img2_w;     // max(H,W) x pitch words: its transpose for the horizontal pass
+  uint16_t *E;          // max(H,W) x pe energies (column 0 at E + E_PADL)
+  uint32_t *Mrow;       // (ceil(max(H,W)/KS) + 1) x pe saved cost rows (column 0 at Mrow + E_PADL)
+  int32_t *seam;        // max(H,W)
+  uint32_t *patch;      // max(H,W)
+};
+
+// width a CTA of nw compute warps with tile height kt covers
+inline int batch_width_limit(int nw, int kt) { return nw * (128 - 2 * kt); }
+
+cudaError_t launch_batch(int nw, int kt, const BatchItem *items, int n, int Smax, int grid, int *queue, int *err,
+                         cudaStream_t st);
+size_t batch_smem_bytes(int nw, int kt, int Smax);
+int batch_blocks_per_sm(int nw, int kt, int Smax);   // after the kernel's smem attribute is set
+
+}  // namespace sc

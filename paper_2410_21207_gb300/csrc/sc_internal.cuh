@@ -17,15 +17,14 @@ namespace sc {
 constexpr int E_PADL = 256;    // left pad (elements) of E and Mrow rows
 constexpr int E_PADR = 1024;   // right pad (elements)
 
-// Seam-search geometry (sc_dp.cu). A lane owns V consecutive columns; a warp's window is
-// 32*V columns, of which Q = 32*V - 2*KT are its own strip; windows exchange boundary rows every
-// KT rows inside a CTA (shared memory) and every K2 rows between the CTAs of a cluster (DSMEM).
-// Ancestors are tracked over super-tiles of KS rows.
+// Seam-search geometry (sc_search.cuh). A lane owns V consecutive columns; a warp's window is
+// 32*V columns, of which 32*V - 2*KT are its own strip; windows exchange boundary rows every KT
+// rows inside a CTA (shared memory) and every K2 rows between the CTAs of a cluster (DSMEM).
+// Ancestors are tracked over super-tiles of KS rows. The cluster path uses KT = DP_KT.
 constexpr int V = 4;
-constexpr int KT = 16;
-constexpr int Q = 32 * V - 2 * KT;   // 96
 constexpr int KS = 64;
 constexpr int K2 = 64;
+constexpr int DP_KT = 16;
 constexpr int MAX_CLUSTER = 16;
 
 // Error bits recorded on the device.

@@ -2,6 +2,7 @@
 // local energy refresh and row compaction (arXiv 2410.21207, sections "Energy Mapping" and
 // "Removal of Seams"; horizontal seams by transposition, section "Design Techniques").
 #include "sc_internal.cuh"
+#include "sc_rowops.cuh"
 
 namespace sc {
 
@@ -10,12 +11,8 @@ __global__ void k_pack(const uint8_t *__restrict__ src, int H, int W, int C, uin
                        int pitch) {
   const int64_t n = (int64_t)H * W;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    const uint8_t *s = src + p * C;
-    uint32_t w = s[0];
-    if (C >= 3) w |= ((uint32_t)s[1] << 8) | ((uint32_t)s[2] << 16);
-    if (C == 4) w |= (uint32_t)s[3] << 24;
     const int i = (int)(p / W), j = (int)(p % W);
-    img[(int64_t)i * pitch + j] = w;
+    img[(int64_t)i * pitch + j] = pack_pixel(src + p * C, C);
   }
 }
 
@@ -24,11 +21,7 @@ __global__ void k_unpack(const uint32_t *__restrict__ img, int pitch, int H, int
   const int64_t n = (int64_t)H * W;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(p / W), j = (int)(p % W);
-    const uint32_t w = img[(int64_t)i * pitch + j];
-    uint8_t *d = dst + p * C;
-    d[0] = (uint8_t)w;
-    if (C >= 3) { d[1] = (uint8_t)(w >> 8); d[2] = (uint8_t)(w >> 16); }
-    if (C == 4) d[3] = (uint8_t)(w >> 24);
+    unpack_pixel(img[(int64_t)i * pitch + j], dst + p * C, C);
   }
 }
 
@@ -49,18 +42,12 @@ __global__ void k_transpose(const uint32_t *__restrict__ src, int ps, int H, int
 }
 
 // ---- e1 energy: sum over the packed channels of |right - left| + |down - up|, clamped ----
-__device__ __forceinline__ uint32_t sad4(uint32_t a, uint32_t b) { return __vsadu4(a, b); }
-
 __global__ void k_energy(const uint32_t *__restrict__ img, int pitch, int H, int W, uint16_t *__restrict__ E,
                          int pe) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y;
   if (j >= W || i >= H) return;
-  const uint32_t *row = img + (int64_t)i * pitch;
-  const int jl = j > 0 ? j - 1 : 0, jr = j + 1 < W ? j + 1 : W - 1;
-  const int iu = i > 0 ? i - 1 : 0, id = i + 1 < H ? i + 1 : H - 1;
-  const uint32_t e = sad4(row[jr], row[jl]) + sad4(img[(int64_t)id * pitch + j], img[(int64_t)iu * pitch + j]);
-  E[(int64_t)i * pe + j] = (uint16_t)e;
+  E[(int64_t)i * pe + j] = (uint16_t)energy_at(img, pitch, H, W, i, j);
 }
 
 // ---- caller energy -> padded layout, with the range check of the 24-bit cost field ----
@@ -84,54 +71,17 @@ __global__ void k_unpad_energy(const uint16_t *__restrict__ E, int pe, int H, in
   dst[(int64_t)i * W + j] = E[(int64_t)i * pe + j];
 }
 
-// ---- local refresh: the two energies per row that the removal changes ----
-// After deleting seam s from a W-wide image, the energy of the (W-1)-wide image equals the old
-// energy shifted left past s_i in row i, except at the new columns s_i - 1 and s_i (the pixels
-// whose left/right neighbour changed, and — since |s_i - s_(i+-1)| <= 1 — the only ones whose
-// upper/lower neighbour can change). This kernel computes those two values from the old image
-// seen through the removal: new pixel (r, j) = old pixel (r, j + [j >= s_r]).
+// ---- local refresh: the two energies per row that the removal changes (patch_row) ----
 __global__ void k_patch(const uint32_t *__restrict__ img, int pitch, int H, int W, const int32_t *__restrict__ seam,
                         uint32_t *__restrict__ patch, int *err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= H) return;
-  const int Wn = W - 1;
-  const int s = seam[i];
-  if (s < 0 || s >= W) { atomicOr(err, ERR_BAD_SEAM); patch[i] = 0; return; }
-  auto pix = [&](int r, int j) -> uint32_t {
-    r = r < 0 ? 0 : (r >= H ? H - 1 : r);
-    j = j < 0 ? 0 : (j >= Wn ? Wn - 1 : j);
-    const int sr = seam[r];
-    return img[(int64_t)r * pitch + j + (j >= sr ? 1 : 0)];
-  };
-  auto en = [&](int j) -> uint32_t { return sad4(pix(i, j + 1), pix(i, j - 1)) + sad4(pix(i + 1, j), pix(i - 1, j)); };
-  const uint32_t p0 = (s >= 1) ? en(s - 1) : 0u;
-  const uint32_t p1 = (s <= Wn - 1) ? en(s) : 0u;
-  patch[i] = p0 | (p1 << 16);
+  bool bad = false;
+  patch[i] = patch_row(img, pitch, H, W, seam, i, &bad);
+  if (bad) atomicOr(err, ERR_BAD_SEAM);
 }
 
-// ---- compaction: every row's tail shifts left by one past the seam (image words and energy),
-// then the two refreshed energies are written. One warp per row; the shift runs left to right in
-// chunks, each chunk read completely before it is written, so it is safe in place. ----
-template <typename T>
-__device__ __forceinline__ void shift_row(T *row, int s, int W, int lane) {
-  constexpr int R = 8;
-  for (int base = s; base < W - 1; base += 32 * R) {
-    T x[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int j = base + r * 32 + lane;
-      x[r] = (j + 1 < W) ? row[j + 1] : T(0);
-    }
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int j = base + r * 32 + lane;
-      if (j < W - 1) row[j] = x[r];
-    }
-    __syncwarp();
-  }
-}
-
+// ---- compaction: one warp per row, in place (compact_row) ----
 __global__ void k_shift(uint32_t *__restrict__ img, int pitch, uint16_t *__restrict__ E, int pe, int H, int W,
                         const int32_t *__restrict__ seam, const uint32_t *__restrict__ patch) {
   const int lane = threadIdx.x & 31;
@@ -139,14 +89,7 @@ __global__ void k_shift(uint32_t *__restrict__ img, int pitch, uint16_t *__restr
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < H; i += warps) {
     const int s = seam[i];
     if (s < 0 || s >= W) continue;   // recorded by k_patch
-    shift_row(img + (int64_t)i * pitch, s, W, lane);
-    uint16_t *er = E + (int64_t)i * pe;
-    shift_row(er, s, W, lane);
-    if (lane == 0) {
-      const uint32_t p = patch[i];
-      if (s >= 1) er[s - 1] = (uint16_t)(p & 0xFFFFu);
-      if (s <= W - 2) er[s] = (uint16_t)(p >> 16);
-    }
+    compact_row(img, pitch, E, pe, W, s, patch[i], i, lane);
   }
 }
 

@@ -1,0 +1,473 @@
+// The minimum-vertical-seam search (arXiv 2410.21207, section "DP Seam Carving": Algorithm 3 and
+// the recurrence M(i,j) = e(i,j) + min(M(i-1,j-1), M(i-1,j), M(i-1,j+1)); the paper's "GPU" variant
+// parallelises the j loop, this code does that and more) as a device function that one CTA, or
+// every CTA of a thread-block cluster, calls together.
+//
+// Layout of the work
+//   * Columns are split over the CTAs (CTA r owns [r*OWC, (r+1)*OWC)) and, inside a CTA, over
+//     NW compute warps; a lane holds V = 4 consecutive columns of the current cost row in registers
+//     and reads its neighbours' edge values with warp shuffles.
+//   * Row-blocked trapezoidal tiles: a warp computes a window of 32*V columns (its strip of
+//     Q = 32*V - 2*KT columns plus KT halo columns per side) for KT rows without talking to other
+//     warps (the valid part shrinks by one column per row), then the strips' last rows are
+//     exchanged through shared memory. One level up (clusters only), each CTA computes K2 halo
+//     columns on either side of its own range and every K2 rows pushes its edge columns into the
+//     neighbours' shared memory with st.async; there is no cluster-wide barrier in the row loop.
+//   * A cost travels with an ancestor: key = (M << 8) | a, with a the column (in the warp's frame)
+//     where the cell's optimal path crossed the top of the current super-tile of KS rows. The
+//     unsigned minimum of three keys is the minimum M and, among equal M, the smallest ancestor.
+//     Optimal predecessors never cross under the leftmost tie-break (pred(j) <= pred(j+1): if
+//     pred(j) = j+1 then M(j+1) < M(j), so j+1 cannot pick j), hence ancestors are non-decreasing
+//     in the column and the smallest ancestor among tied candidates is the leftmost candidate's:
+//     the key minimum carries exactly Algorithm 3's choice. The bottom row of each super-tile
+//     records its ancestors; a chain of ceil(H/KS) lookups gives the seam column at every
+//     super-tile boundary, and then the super-tiles are backtracked in parallel by recomputing
+//     their KS rows in a 256-column window from a saved cost row with explicit directions.
+//   * Energies are staged in shared memory by TMA: a producer warp issues one bulk copy per row
+//     (one row per lane) into an NSLOT-slot ring, gated by full/empty mbarriers; a lane reads its 4
+//     energies of a row with one 8-byte shared-memory load.
+//   * The rows of a full tile are branch-free; row 0 and a ragged last tile take a general path,
+//     and per-super-tile bookkeeping runs after the tile, on its last row (the only row of a full
+//     tile where it can occur, since KS is a multiple of KT).
+// The result is Algorithm 3's seam exactly (leftmost ties, leftmost last-row minimum).
+#pragma once
+#include <cooperative_groups.h>
+
+#include "sc_internal.cuh"
+#include "sc_ptx.cuh"
+
+namespace sc {
+
+namespace cg = cooperative_groups;
+
+constexpr uint32_t SENT = 0xFFFFFFFFu;   // excluded (outside the image): above every key
+constexpr int FILL_W = 256;              // backtrack-fill window (8 columns per lane)
+constexpr int FILL_WARPS_MAX = 8;        // warps that run backtrack fills
+constexpr int NSLOT = 3;                 // energy staging ring: tiles in flight
+
+template <int NW, int KT, bool CL>
+struct Geo {
+  static constexpr int Q = 32 * V - 2 * KT;              // warp strip
+  static constexpr int K2E = CL ? K2 : 0;                // CTA-level halo (clusters only)
+  static constexpr int BW = NW * Q + 2 * KT;             // boundary / staged row width
+  static constexpr int OWC = NW * Q - 2 * K2E;           // CTA-own columns
+  static constexpr int FW = (NW + 1) < FILL_WARPS_MAX ? (NW + 1) : FILL_WARPS_MAX;
+  static constexpr int THREADS = (NW + 1) * 32;          // compute warps + the producer warp
+  static_assert(Q > 0 && KS % KT == 0 && K2 % KT == 0, "tile geometry");
+  static_assert(Q + 2 * KS <= 256, "the ancestor frame must fit 8 bits");
+};
+
+// offsets of the dynamic shared-memory regions used by seam_search
+struct SearchPlan {
+  size_t bnd, hbuf, anc, wmin, cmin, jb, misc, fdir, ring, bars, total;
+};
+
+template <int NW, int KT, bool CL>
+__host__ __device__ inline SearchPlan search_plan(int S) {
+  using G = Geo<NW, KT, CL>;
+  SearchPlan p;
+  size_t o = 0;
+  p.bnd = o;  o += (size_t)2 * G::BW * 4;  o = (o + 15) & ~(size_t)15;
+  p.hbuf = o; o += CL ? (size_t)2 * 2 * K2 * 4 : 0;
+  p.anc = o;  o += (size_t)S * G::OWC;  o = (o + 15) & ~(size_t)15;
+  p.wmin = o; o += (size_t)(NW + 1) * 8;
+  p.cmin = o; o += 8;
+  p.jb = o;   o += (size_t)(S + 1) * 4;  o = (o + 15) & ~(size_t)15;
+  p.misc = o; o += 16;
+  p.fdir = o; o += (size_t)G::FW * KS * 32 * 2;  o = (o + 15) & ~(size_t)15;
+  p.ring = o; o += (size_t)NSLOT * KT * G::BW * 2;  o = (o + 15) & ~(size_t)15;
+  p.bars = o; o += (size_t)(2 * NSLOT + 2) * 8;   // full[NSLOT], empty[NSLOT], halo[2]
+  p.total = (o + 15) & ~(size_t)15;
+  return p;
+}
+
+struct SearchArgs {
+  const uint16_t *E;   // row 0, column 0 (already offset by E_PADL)
+  int pitch_e;
+  int H, W;
+  uint32_t *Mrow;      // super-tile boundary cost rows, row s at Mrow + s*pitch_e (offset by E_PADL)
+  int32_t *seam;       // out [H]
+  int32_t *seam_log;   // nullable, out [H]
+  int64_t *cost;       // nullable, out [1]
+  int *err;            // device error word
+  bool gated;          // skip the search (energy range failure)
+};
+
+// Running counters of the mbarrier phases, identical in every thread of the CTA.
+struct SearchState {
+  uint32_t tiles = 0;  // tiles staged so far (ring slot and phase)
+  uint32_t exch = 0;   // inter-CTA exchanges so far (halo buffer and phase)
+};
+
+__device__ __forceinline__ uint32_t min3u(uint32_t a, uint32_t b, uint32_t c) { return __vimin3_u32(a, b, c); }
+
+// (uint16 pair) -> value << 8 for the low / high half
+__device__ __forceinline__ uint32_t lo8(uint32_t x) { return __byte_perm(x, 0u, 0x4104); }
+__device__ __forceinline__ uint32_t hi8(uint32_t x) { return __byte_perm(x, 0u, 0x4324); }
+
+// Bookkeeping after row i (keys k of this lane's V columns, warp frame base fb):
+//  - bottom of a super-tile: record the ancestors of the CTA-own columns (one byte: a - col + 128);
+//  - last row before a super-tile: save the raw cost row for the backtrack fill;
+//  - last row of the image: fold the lane's (M << 32 | column) minimum.
+__device__ __forceinline__ void row_events(int i, const uint32_t (&k)[V], int H, int W, int c0, int fb, bool cta_own,
+                                           int A, uint32_t *__restrict__ Mrow, int pitch_e,
+                                           uint8_t *__restrict__ ancT, int OWC, unsigned long long &lastmin) {
+  if (!cta_own) return;
+  if (((i + 1) % KS == 0) || (i == H - 1)) {
+    const uint32_t d = (uint32_t)(fb - c0 + 128);
+    const uint32_t a = ((k[0] + d) & 0xFFu) | (((k[1] + d - 1u) & 0xFFu) << 8) | (((k[2] + d - 2u) & 0xFFu) << 16) |
+                       (((k[3] + d - 3u) & 0xFFu) << 24);
+    *reinterpret_cast<uint32_t *>(ancT + (size_t)(i / KS) * OWC + (c0 - A)) = a;
+  }
+  if (((i + 1) % KS == 0) && (i + 1 < H)) {
+    uint4 m;
+    m.x = k[0] >> 8; m.y = k[1] >> 8; m.z = k[2] >> 8; m.w = k[3] >> 8;
+    *reinterpret_cast<uint4 *>(Mrow + (size_t)((i + 1) / KS) * pitch_e + c0) = m;
+  }
+  if (i == H - 1) {
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      if (c0 + u < W) {
+        const unsigned long long c = ((unsigned long long)(k[u] >> 8) << 32) | (unsigned)(c0 + u);
+        lastmin = c < lastmin ? c : lastmin;
+      }
+    }
+  }
+}
+
+// One DP row for a lane: keys k (previous row) -> next row; energies ev (4 x uint16).
+__device__ __forceinline__ void dp_row(uint32_t (&k)[V], uint2 ev, const uint32_t (&oobm)[V]) {
+  const uint32_t e0 = lo8(ev.x), e1 = hi8(ev.x), e2 = lo8(ev.y), e3 = hi8(ev.y);
+  const uint32_t L = __shfl_up_sync(0xffffffffu, k[V - 1], 1);
+  const uint32_t R = __shfl_down_sync(0xffffffffu, k[0], 1);
+  const uint32_t n0 = (min3u(L, k[0], k[1]) + e0) | oobm[0];
+  const uint32_t n1 = (min3u(k[0], k[1], k[2]) + e1) | oobm[1];
+  const uint32_t n2 = (min3u(k[1], k[2], k[3]) + e2) | oobm[2];
+  const uint32_t n3 = (min3u(k[2], k[3], R) + e3) | oobm[3];
+  k[0] = n0; k[1] = n1; k[2] = n2; k[3] = n3;
+}
+
+// Initialise the staging and halo mbarriers (thread 0; the caller then synchronises the CTA, and
+// the cluster when CL).
+template <int NW, int KT, bool CL>
+__device__ inline void search_init(unsigned char *smem, int S) {
+  const SearchPlan plan = search_plan<NW, KT, CL>(S);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + plan.bars);
+  uint64_t *empty = full + NSLOT;
+  uint64_t *hbar = empty + NSLOT;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NSLOT; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], NW);
+    }
+    mbar_init(&hbar[0], 1);
+    mbar_init(&hbar[1], 1);
+    fence_mbar_init();
+  }
+}
+
+template <bool CL>
+__device__ __forceinline__ void group_sync() {
+  if (CL) cg::this_cluster().sync(); else __syncthreads();
+}
+
+// The search. Every thread of the CTA (of every CTA of the cluster when CL) calls it with the same
+// arguments; `Smax` is the super-tile count the shared-memory plan was sized for.
+template <int NW, int KT, bool CL>
+__device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, SearchState &st) {
+  using G = Geo<NW, KT, CL>;
+  constexpr int Q = G::Q, BW = G::BW, OWC = G::OWC, K2E = G::K2E;
+  const int rank = CL ? (int)cg::this_cluster().block_rank() : 0;
+  const int cs = CL ? (int)cg::this_cluster().num_blocks() : 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool producer = (warp == NW);
+  const int H = p.H, W = p.W;
+  const int S = (H + KS - 1) / KS;
+  const SearchPlan plan = search_plan<NW, KT, CL>(Smax);
+  uint32_t *bnd = reinterpret_cast<uint32_t *>(smem + plan.bnd);
+  uint32_t *hbuf = reinterpret_cast<uint32_t *>(smem + plan.hbuf);
+  uint8_t *ancT = reinterpret_cast<uint8_t *>(smem + plan.anc);
+  unsigned long long *wmin = reinterpret_cast<unsigned long long *>(smem + plan.wmin);
+  unsigned long long *cmin = reinterpret_cast<unsigned long long *>(smem + plan.cmin);
+  int *jb = reinterpret_cast<int *>(smem + plan.jb);
+  int *misc = reinterpret_cast<int *>(smem + plan.misc);
+  uint16_t *fdir = reinterpret_cast<uint16_t *>(smem + plan.fdir);
+  uint16_t *ring = reinterpret_cast<uint16_t *>(smem + plan.ring);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + plan.bars);
+  uint64_t *empty = full + NSLOT;
+  uint64_t *hbar = empty + NSLOT;
+
+  // geometry
+  const int A = rank * OWC, B = A + OWC;
+  const int ext0 = A - K2E;                     // extended range start
+  const int own0 = ext0 + warp * Q;             // warp strip start
+  const int c0 = own0 - KT + lane * V;          // this lane's first column
+  const int frame_base = own0 - KS;             // ancestor frame of this warp
+  const bool strip_lane = !producer && (lane * V >= KT) && (lane * V < KT + Q);
+  const bool cta_own = strip_lane && c0 >= A && c0 < B;   // A, B, c0 are multiples of 4
+  uint32_t oobm[V];
+#pragma unroll
+  for (int u = 0; u < V; ++u) oobm[u] = (c0 + u < 0 || c0 + u >= W) ? SENT : 0u;
+  const int bidx0 = c0 - (ext0 - KT);           // index of c0 in bnd and in a staged energy row
+
+  unsigned long long lastmin = ~0ull;
+  const int nt = p.gated ? 0 : (H + KT - 1) / KT;
+  constexpr uint32_t ROW_BYTES = BW * 2;
+
+  if (producer) {
+    // ---- energy staging: rows of columns [ext0 - KT, ext0 - KT + BW), one bulk copy per lane ----
+    const uint16_t *Estage = p.E + (ext0 - KT);
+    for (int tt = 0; tt < nt; ++tt) {
+      const uint32_t g = st.tiles + tt;
+      const int slot = (int)(g % NSLOT);
+      if (g >= NSLOT && !mbar_wait_bounded(&empty[slot], ((g / NSLOT) - 1) & 1u, WAIT_TIMEOUT_NS)) {
+        if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
+      }
+      const int rbeg = tt * KT;
+      const int nrows = (H - rbeg < KT) ? H - rbeg : KT;
+      if (lane == 0) mbar_arrive_expect_tx(&full[slot], (uint32_t)nrows * ROW_BYTES);
+      __syncwarp();
+      if (lane < nrows)
+        bulk_g2s(ring + (size_t)(slot * KT + lane) * BW, Estage + (size_t)(rbeg + lane) * p.pitch_e, ROW_BYTES,
+                 &full[slot]);
+    }
+  } else {
+    uint32_t k[V] = {0u, 0u, 0u, 0u};
+    for (int t = 0; t < nt; ++t) {
+      const int r0 = t * KT;
+      const bool more = r0 + KT < H;
+      const uint32_t g = st.tiles + t;
+      const int slot = (int)(g % NSLOT);
+      if (!mbar_wait_bounded(&full[slot], (g / NSLOT) & 1u, WAIT_TIMEOUT_NS)) {
+        if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
+      }
+      const uint16_t *er = ring + (size_t)slot * KT * BW + bidx0;
+      if (t > 0) {
+        // window of the previous row from the boundary buffer (relative ancestors -> warp frame)
+        const uint4 v = *reinterpret_cast<const uint4 *>(bnd + ((t - 1) & 1) * BW + bidx0);
+        if (r0 % KS == 0) {
+          // a new super-tile: every cell becomes its own ancestor. The old ancestor field is
+          // dropped without arithmetic: it may lie outside this warp's frame.
+          const uint32_t a = (uint32_t)(c0 - frame_base);
+          k[0] = (v.x & ~0xFFu) | a; k[1] = (v.y & ~0xFFu) | (a + 1);
+          k[2] = (v.z & ~0xFFu) | (a + 2); k[3] = (v.w & ~0xFFu) | (a + 3);
+        } else {
+          // relative ancestor -> this warp's frame (exact for every cell that can reach the strip)
+          const uint32_t d = (uint32_t)(c0 - frame_base) - 128u;
+          k[0] = v.x + d; k[1] = v.y + d + 1u; k[2] = v.z + d + 2u; k[3] = v.w + d + 3u;
+        }
+        k[0] |= oobm[0]; k[1] |= oobm[1]; k[2] |= oobm[2]; k[3] |= oobm[3];
+      }
+      if (t > 0 && !(r0 + KT > H)) {
+        // full tile: KT branch-free rows, bookkeeping only on its last row
+#pragma unroll
+        for (int r = 0; r < KT; ++r) dp_row(k, *reinterpret_cast<const uint2 *>(er + r * BW), oobm);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);   // this warp is done with the staged rows
+        row_events(r0 + KT - 1, k, H, W, c0, frame_base, cta_own, A, p.Mrow, p.pitch_e, ancT, OWC, lastmin);
+      } else {
+        // first tile (row 0 has no predecessor) or a ragged last tile
+        for (int r = 0; r < KT; ++r) {
+          const int i = r0 + r;
+          if (i >= H) break;
+          const uint2 ev = *reinterpret_cast<const uint2 *>(er + r * BW);
+          if (i == 0) {
+            const uint32_t a = (uint32_t)(c0 - frame_base);
+            k[0] = (lo8(ev.x) | a) | oobm[0];
+            k[1] = (hi8(ev.x) | (a + 1)) | oobm[1];
+            k[2] = (lo8(ev.y) | (a + 2)) | oobm[2];
+            k[3] = (hi8(ev.y) | (a + 3)) | oobm[3];
+          } else {
+            dp_row(k, ev, oobm);
+          }
+          row_events(i, k, H, W, c0, frame_base, cta_own, A, p.Mrow, p.pitch_e, ancT, OWC, lastmin);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+      }
+      if (more) {
+        const bool exch = CL && ((r0 + KT) % K2 == 0) && cs > 1;
+        const uint32_t d = (uint32_t)(c0 - frame_base) - 128u;
+        uint4 v;
+        v.x = k[0] - d; v.y = k[1] - d - 1u; v.z = k[2] - d - 2u; v.w = k[3] - d - 3u;
+        // publish this warp's strip (relative ancestor encoding); at an exchange the CTA's halo
+        // columns come from the neighbours instead
+        if (strip_lane && (!exch || (c0 >= A && c0 < B)))
+          *reinterpret_cast<uint4 *>(bnd + (t & 1) * BW + bidx0) = v;
+        if (CL && exch) {
+          const uint32_t xg = st.exch + (uint32_t)((r0 + KT) / K2 - 1);
+          const int par = (int)(xg & 1);
+          // my first K2 own columns are the left neighbour's right halo, my last K2 the right's left
+          if (strip_lane && rank > 0 && c0 >= A && c0 < A + K2)
+            st_async_v4(mapa_u32(hbuf + par * 2 * K2 + K2 + (c0 - A), rank - 1), v, mapa_u32(&hbar[par], rank - 1));
+          if (strip_lane && rank < cs - 1 && c0 >= B - K2 && c0 < B)
+            st_async_v4(mapa_u32(hbuf + par * 2 * K2 + (c0 - (B - K2)), rank + 1), v, mapa_u32(&hbar[par], rank + 1));
+          if (threadIdx.x == 0)
+            mbar_arrive_expect_tx(&hbar[par], (uint32_t)(((rank > 0) + (rank < cs - 1)) * K2 * 4));
+          if (!mbar_wait_bounded(&hbar[par], (xg >> 1) & 1u, WAIT_TIMEOUT_NS)) {
+            if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
+          }
+          uint32_t *mine = bnd + (t & 1) * BW;
+          for (int q = threadIdx.x; q < 2 * K2; q += NW * 32) {
+            if (q < K2) {
+              if (rank > 0) mine[(A - K2 + q) - (ext0 - KT)] = hbuf[par * 2 * K2 + q];
+            } else {
+              if (rank < cs - 1) mine[(B + (q - K2)) - (ext0 - KT)] = hbuf[par * 2 * K2 + q];
+            }
+          }
+        }
+        named_bar_sync(NW * 32);
+      }
+    }
+  }
+  st.tiles += (uint32_t)nt;
+  if (CL && nt > 0) st.exch += (uint32_t)((cs > 1) ? ((H - 1) / K2) : 0);
+
+  // ---- last-row argmin: the leftmost minimum (min of (M << 32) | column) ----
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, lastmin, off);
+    lastmin = o < lastmin ? o : lastmin;
+  }
+  if (lane == 0) wmin[warp] = lastmin;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = ~0ull;
+    for (int w = 0; w <= NW; ++w) m = wmin[w] < m ? wmin[w] : m;
+    *cmin = m;
+  }
+  group_sync<CL>();
+
+  // ---- ancestor chain (rank 0, one thread): seam column at every super-tile bottom ----
+  if (rank == 0 && threadIdx.x == 0) {
+    int ok = !p.gated;
+    unsigned long long best = ~0ull;
+    for (int r = 0; r < cs; ++r) {
+      const unsigned long long *rm = CL ? cg::this_cluster().map_shared_rank(cmin, r) : cmin;
+      best = *rm < best ? *rm : best;
+    }
+    int j = (int)(best & 0xFFFFFFFFull);
+    if (ok && (j < 0 || j >= W)) { ok = 0; atomicOr(p.err, ERR_BAD_SEAM); }
+    for (int s = S - 1; ok && s >= 0; --s) {
+      jb[s] = j;
+      const int c = j / OWC;
+      if (c < 0 || c >= cs) { ok = 0; atomicOr(p.err, ERR_BAD_SEAM); break; }
+      const uint8_t *ra = CL ? cg::this_cluster().map_shared_rank(ancT, c) : ancT;
+      j = j + (int)ra[(size_t)s * OWC + (j - c * OWC)] - 128;
+      if (j < 0 || j >= W) { ok = 0; atomicOr(p.err, ERR_BAD_SEAM); }
+    }
+    jb[S] = j;          // the seam's column in row 0
+    misc[0] = ok;
+    misc[1] = (int)(best >> 32);
+    if (ok && p.cost) *p.cost = (int64_t)(best >> 32);
+  }
+  group_sync<CL>();
+
+  // ---- parallel backtrack: each super-tile recomputed in a 256-column window ----
+  const int *jb0 = CL ? cg::this_cluster().map_shared_rank(jb, 0) : jb;
+  const int *misc0 = CL ? cg::this_cluster().map_shared_rank(misc, 0) : misc;
+  const int ok = misc0[0];
+  const uint32_t best_m = (uint32_t)misc0[1];
+  uint16_t *fd = fdir + (size_t)warp * KS * 32;
+  for (int s = warp * cs + rank; ok && warp < G::FW && s < S; s += G::FW * cs) {
+    const int jbs = jb0[s];
+    const int jprev = (s > 0) ? jb0[s - 1] : jb0[S];
+    int x0 = jbs - 128;
+    x0 -= ((x0 % 8) + 8) % 8;
+    const int xc = x0 + lane * 8;
+    const int rs = s * KS, re = (rs + KS < H) ? rs + KS : H;
+    const int first = (s == 0) ? 1 : rs;
+    uint32_t m[8], oob[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) oob[u] = (xc + u < 0 || xc + u >= W) ? SENT : 0u;
+    if (s == 0) {
+      const uint4 ev = *reinterpret_cast<const uint4 *>(p.E + xc);
+      m[0] = ev.x & 0xFFFFu; m[1] = ev.x >> 16; m[2] = ev.y & 0xFFFFu; m[3] = ev.y >> 16;
+      m[4] = ev.z & 0xFFFFu; m[5] = ev.z >> 16; m[6] = ev.w & 0xFFFFu; m[7] = ev.w >> 16;
+    } else {
+      const uint4 a = *reinterpret_cast<const uint4 *>(p.Mrow + (size_t)s * p.pitch_e + xc);
+      const uint4 b = *reinterpret_cast<const uint4 *>(p.Mrow + (size_t)s * p.pitch_e + xc + 4);
+      m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w; m[4] = b.x; m[5] = b.y; m[6] = b.z; m[7] = b.w;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) m[u] |= oob[u];
+    // rows first..re-1 in chunks of 4 with the next chunk's energies loaded ahead
+    constexpr int CH = 4;
+    uint4 eb0[CH], eb1[CH];
+    auto load_chunk = [&](uint4 (&eb)[CH], int rbeg) {
+#pragma unroll
+      for (int r = 0; r < CH; ++r) {
+        const int i = rbeg + r;
+        if (i < re) eb[r] = *reinterpret_cast<const uint4 *>(p.E + (size_t)i * p.pitch_e + xc);
+      }
+    };
+    auto run_chunk = [&](const uint4 (&eb)[CH], int rbeg) {
+#pragma unroll
+      for (int r = 0; r < CH; ++r) {
+        const int i = rbeg + r;
+        if (i >= re) break;
+        const uint32_t ee[8] = {eb[r].x & 0xFFFFu, eb[r].x >> 16, eb[r].y & 0xFFFFu, eb[r].y >> 16,
+                                eb[r].z & 0xFFFFu, eb[r].z >> 16, eb[r].w & 0xFFFFu, eb[r].w >> 16};
+        const uint32_t L = __shfl_up_sync(0xffffffffu, m[7], 1);
+        const uint32_t R = __shfl_down_sync(0xffffffffu, m[0], 1);
+        uint32_t nm[8];
+        uint32_t dirs = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const uint32_t a = (u == 0) ? L : m[u - 1];
+          const uint32_t b = m[u];
+          const uint32_t c = (u == 7) ? R : m[u + 1];
+          const uint32_t mn = min3u(a, b, c);
+          const uint32_t dd = (a == mn) ? 0u : ((b == mn) ? 1u : 2u);
+          dirs |= dd << (2 * u);
+          nm[u] = (mn + ee[u]) | oob[u];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) m[u] = nm[u];
+        fd[(i - rs) * 32 + lane] = (uint16_t)dirs;
+      }
+    };
+    int rb = first;
+    load_chunk(eb0, rb);
+    while (rb < re) {
+      if (rb + CH < re) load_chunk(eb1, rb + CH);
+      run_chunk(eb0, rb);
+      rb += CH;
+      if (rb >= re) break;
+      if (rb + CH < re) load_chunk(eb0, rb + CH);
+      run_chunk(eb1, rb);
+      rb += CH;
+    }
+    if (s == S - 1) {
+      // the recomputed cost at the bottom of the seam must be the argmin's
+      const int rel = jbs - x0;
+      if ((rel >> 3) == lane) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) if (u == (rel & 7)) v = m[u];
+        if (v != best_m) atomicOr(p.err, ERR_COST_MISMATCH);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      int j = jbs;
+      for (int i = re - 1; i >= first; --i) {
+        p.seam[i] = j;
+        if (p.seam_log) p.seam_log[i] = j;
+        const int rel = j - x0;
+        if (rel < 0 || rel >= FILL_W) { atomicOr(p.err, ERR_FILL_MISMATCH); j = -1; break; }
+        const uint32_t dd = (fd[(i - rs) * 32 + (rel >> 3)] >> (2 * (rel & 7))) & 3u;
+        j += (int)dd - 1;
+      }
+      if (s == 0 && j >= 0) {
+        p.seam[0] = j;
+        if (p.seam_log) p.seam_log[0] = j;
+      }
+      if (j != jprev) atomicOr(p.err, ERR_FILL_MISMATCH);
+    }
+    __syncwarp();
+  }
+  group_sync<CL>();   // rank 0's shared memory is read above; the seam is complete after this
+}
+
+}  // namespace sc

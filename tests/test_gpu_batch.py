@@ -1,0 +1,83 @@
+"""The batched persistent form (sc_carve_batch, batch plans): every image equals the oracle's carve
+of that image alone, byte for byte, including the seam log."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_21207_gb300 import binding as sc
+from paper_2410_21207_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.fail("the -m gpu tests need a CUDA GPU")
+    return torch.device("cuda:0")
+
+
+def _mixed_batch(rng):
+    imgs, targets = [], []
+    shapes = [(1, 1, 3), (2, 3, 1), (5, 40, 4), (40, 7, 3), (61, 97, 3), (180, 240, 3), (33, 1000, 3),
+              (300, 700, 1), (100, 1500, 3), (70, 2000, 3), (1500, 90, 3)]
+    for H, W, C in shapes:
+        if rng.random() < 0.3:
+            img = rng.integers(0, 3, size=(H, W, C)).astype(np.uint8)      # many exact ties
+        else:
+            img = rng.integers(0, 256, size=(H, W, C)).astype(np.uint8)
+        tw = int(rng.integers(max(1, W // 2), W + 1))
+        th = int(rng.integers(max(1, (3 * H) // 4), H + 1))
+        imgs.append(img)
+        targets.append((tw, th))
+    return imgs, targets
+
+
+def _check(imgs, targets, outs, logs):
+    for img, (tw, th), o, lg in zip(imgs, targets, outs, logs):
+        r_out, r_log, _ = oracle.carve(img, tw, th, with_log=True)
+        np.testing.assert_array_equal(o.cpu().numpy().reshape(r_out.shape), r_out)
+        np.testing.assert_array_equal(lg.cpu().numpy()[: len(r_log)], r_log)
+
+
+def test_batch_mixed_sizes_equal_alone(dev):
+    """Sizes from 1x1 to 2000 wide, both passes, C in {1,3,4}; the widest go to the cluster path."""
+    rng = np.random.default_rng(404)
+    imgs, targets = _mixed_batch(rng)
+    d = [torch.from_numpy(i).to(dev) for i in imgs]
+    outs, logs = sc.carve_batch(d, targets, with_log=True)
+    sc.check()
+    _check(imgs, targets, outs, logs)
+
+
+def test_batch_config4_subset_equal_alone(dev):
+    jobs = synth.config4(n=24, seed=4)
+    imgs = [j.make() for j in jobs]
+    targets = [(j.target_w, j.target_h) for j in jobs]
+    d = [torch.from_numpy(i).to(dev) for i in imgs]
+    outs, logs = sc.carve_batch(d, targets, with_log=True)
+    sc.check()
+    _check(imgs, targets, outs, logs)
+
+
+def test_batch_plan_autotuned_replays(dev):
+    """An autotuned plan (CUDA graph) replays correctly, also after the inputs change in place."""
+    rng = np.random.default_rng(9)
+    imgs = [synth.gen_image(int(rng.integers(60, 500)), int(rng.integers(40, 300)), 5, 10, 80, 100 + k)
+            for k in range(10)]
+    targets = [(max(1, (4 * im.shape[1]) // 5), im.shape[0] - (k % 3) * 5) for k, im in enumerate(imgs)]
+    d = [torch.from_numpy(i).to(dev) for i in imgs]
+    plan = sc.BatchPlan(d, targets, autotune=True, with_log=True)
+    info = plan.info()
+    assert info["batched"] == len(imgs) and info["cluster_path"] == 0
+    assert info["tile_rows"] in (8, 16, 32)
+    for rep in range(2):
+        plan.run()
+        sc.check()
+        _check(imgs, targets, plan.outs, plan.logs)
+        # new contents, same sizes
+        imgs = [synth.gen_image(im.shape[1], im.shape[0], 5, 10, 80, 500 + rep * 10 + k) for k, im in enumerate(imgs)]
+        for t, im in zip(d, imgs):
+            t.copy_(torch.from_numpy(im))
+    plan.close()
