@@ -39,6 +39,9 @@ def _args():
     ap.add_argument("--plain", action="store_true", help="time the per-seam-launch plain path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched (256-image) measurement")
+    ap.add_argument("--profile-search", metavar="HxW", default=None,
+                    help="only call sc_find_seam a few times on a seeded HxW energy map (for ncu captures)")
     return ap.parse_args()
 
 
@@ -145,6 +148,72 @@ def cpu_baseline(job, img, budget_s: float = 15.0):
                       f"full energy recompute per seam"}
 
 
+def batched_measurement(sc, torch, dev, flush, steps):
+    """Config 4 (256 images, W 240..1280, H 180..960, width -10..40 %) as one autotuned batch plan
+    (persistent kernel in a CUDA graph) against the plain path (one image at a time, per-seam
+    launches) on the first 16 of the same images."""
+    from paper_2410_21207_gb300 import synth
+    jobs = synth.config4()
+    imgs = [torch.from_numpy(j.make()).to(dev) for j in jobs]
+    targets = [(j.target_w, j.target_h) for j in jobs]
+    seams = sum(j.seams for j in jobs)
+    mpix = sum(j.mpix_seams() for j in jobs)
+    plan = sc.BatchPlan(imgs, targets, autotune=True)
+    for _ in range(2):
+        plan.run()
+    sc.check()
+    ms = []
+    for _ in range(max(2, steps)):
+        flush.zero_()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record()
+        plan.run()
+        s1.record()
+        torch.cuda.synchronize(dev)
+        ms.append(s0.elapsed_time(s1))
+    sc.check()
+    info = plan.info()
+    plan.close()
+    bms = statistics.median(ms)
+    sub = list(range(16))
+    sub_seams = sum(jobs[k].seams for k in sub)
+    for k in sub[:2]:
+        sc.carve(imgs[k], *targets[k], plain=True)
+    torch.cuda.synchronize(dev)
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record()
+    for k in sub:
+        sc.carve(imgs[k], *targets[k], plain=True)
+    p1.record()
+    torch.cuda.synchronize(dev)
+    sc.check()
+    plain_sps = sub_seams / (p0.elapsed_time(p1) / 1000.0)
+    batched_sps = seams / (bms / 1000.0)
+    return {"workload": "256 images, W 240..1280, H 180..960, width -10..40 % (seed 4)",
+            "seams_per_batch": seams, "ms_per_batch": bms, "seams_per_s": batched_sps,
+            "mpix_seam_per_s": mpix / (bms / 1000.0), "plan": info,
+            "plain_seams_per_s": plain_sps, "plain_sample": "first 16 images, one image per launch sequence",
+            "batched_over_plain": batched_sps / plain_sps}
+
+
+def profile_search(spec: str):
+    """sc_find_seam four times on a seeded H x W uint16 energy map (the kernel to capture is k_dp)."""
+    import numpy as np
+    import torch
+    from paper_2410_21207_gb300 import binding as sc
+    H, W = (int(x) for x in spec.lower().split("x"))
+    e = np.random.default_rng(0).integers(0, 1531, size=(H, W)).astype(np.uint16)
+    t = torch.from_numpy(e).to("cuda:0")
+    for _ in range(4):
+        sc.find_seam(t)
+    torch.cuda.synchronize()
+    sc.check()
+    print(json.dumps({"profile_search": spec, "ok": True}))
+    return 0
+
+
 def run_reference(a):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -215,23 +284,32 @@ def run_native(a):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    sc.timing_reset()
-    barrier()
-    with ClockSampler(local if ws > 1 else 0) as clk:
-        sc.timing_enable(True)
+    def timed_steps(instrumented: bool):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+        if instrumented:
+            sc.timing_reset()
+            sc.timing_enable(True)
+        barrier()
         for k in range(a.steps):
             flush.zero_()
             starts[k].record()
             step()
             ends[k].record()
         barrier()
-        sc.timing_enable(False)
-    sc.check()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        if instrumented:
+            sc.timing_enable(False)
+        sc.check()
+        return [st.elapsed_time(en) for st, en in zip(starts, ends)]
+
+    # headline: uninstrumented
+    with ClockSampler(local if ws > 1 else 0) as clk:
+        step_ms = timed_steps(False)
+    # the same steps again with the library bracketing every k_dp launch with CUDA events
+    timed_steps(True)
     dp_ms, dp_n = sc.timing_read("dp")
     _, launches = sc.timing_read("all")
+    launches //= max(1, a.steps)
     total_s = sum(step_ms) / 1000.0
     if ws > 1:
         import torch.distributed as dist
@@ -256,7 +334,7 @@ def run_native(a):
                    "l2": "flushed between steps (256 MB write), outside the timed brackets",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "mpix_seam_per_s": mpix * a.steps * ws / total_s,
-        "gpu_launches": int(launches),
+        "gpu_launches": int(launches) * a.steps,
         "roofline": {"kernel": "k_dp (seam search)", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "peak_source": peak_src, "dp_ms_per_launch": dp_ms / max(dp_n, 1),
@@ -275,6 +353,8 @@ def run_native(a):
         e2e_s = statistics.median(t_e2e[1:]) if len(t_e2e) > 1 else t_e2e[0]
         line["e2e"] = {"value": seams / e2e_s, "unit": "seams/s", "h2d_bytes_per_step": H * W * 3,
                        "d2h_bytes_per_step": th * tw * 3}
+    if rank == 0 and not a.no_batched:
+        line["batched"] = batched_measurement(sc, torch, dev, flush, a.steps)
     if rank == 0 and not a.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(job, img_np)
     if rank == 0:
@@ -288,6 +368,8 @@ def run_native(a):
 
 def main():
     a = _args()
+    if a.profile_search:
+        return profile_search(a.profile_search)
     if a.impl == "reference":
         return run_reference(a)
     return run_native(a)

@@ -179,6 +179,37 @@ int sc_batch_plan_run(sc_batch_plan *plan, void *stream);
 int sc_batch_plan_info(const sc_batch_plan *plan, int *nw, int *kt, int *grid, int *batched, int *fallback);
 int sc_batch_plan_destroy(sc_batch_plan *plan);
 
+/* ---- serving form: continuous batching with device-memory admission ----
+ * A server owns one device arena of budget_bytes (the memory ledger) and `streams` CUDA streams
+ * (half carve micro-batches, half carve wide requests on the cluster path). A worker thread admits
+ * queued requests in arrival order whenever the arena and a stream have room: requests that fit
+ * one CTA (searched width <= 1440) are grouped, up to max_batch, into one persistent batched
+ * launch; wider ones are carved alone by the cluster path. Groups on different streams run
+ * concurrently, so requests submitted while others are on the GPU start as soon as memory and a
+ * stream free up. Every result equals sc_carve of that image alone.
+ * sc_server_submit: img_host (H*W*C bytes) and out_host (target_h*target_w*C bytes) are host
+ *   buffers that must stay valid until the request completes; they should be pinned (page-locked),
+ *   otherwise the device->host copy makes the worker wait for that group. Images up to 4096 x 4096.
+ *   Returns a ticket. Errors: SC_EINVAL (as sc_carve), SC_ENOMEM (larger than the whole budget).
+ * sc_server_poll: 1 when done (latency_s = completion - submission, seconds), 0 while pending,
+ *   a negative status if the request failed.
+ * sc_server_drain: waits until nothing is queued or running (SC_ETIMEOUT after timeout_s).
+ * sc_server_stats: counters and latency percentiles over the completed requests. */
+typedef struct sc_server sc_server;
+typedef struct {
+  int64_t completed, queued, in_flight_groups, groups, batched, cluster_path;
+  size_t bytes_in_use, peak_bytes, budget_bytes;
+  int device_errors;
+  double p50_s, p99_s, max_s;
+} sc_server_stats_t;
+int sc_server_create(size_t budget_bytes, int max_batch, int streams, sc_server **server);
+int sc_server_submit(sc_server *server, const uint8_t *img_host, int H, int W, int C, int target_w, int target_h,
+                     uint8_t *out_host, int64_t *ticket);
+int sc_server_poll(sc_server *server, int64_t ticket, double *latency_s);
+int sc_server_drain(sc_server *server, double timeout_s);
+int sc_server_stats(sc_server *server, sc_server_stats_t *stats);
+int sc_server_destroy(sc_server *server);
+
 #ifdef __cplusplus
 }
 #endif

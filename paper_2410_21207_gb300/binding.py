@@ -280,3 +280,88 @@ def timing_read(kernel: str) -> Tuple[float, int]:
     n = ctypes.c_int64(0)
     _raise(load().sc_timing_read(kernel.encode(), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("queued", ctypes.c_int64), ("in_flight_groups", ctypes.c_int64),
+                ("groups", ctypes.c_int64), ("batched", ctypes.c_int64), ("cluster_path", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
+                ("device_errors", ctypes.c_int), ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double),
+                ("max_s", ctypes.c_double)]
+
+
+def _server_sigs(lib):
+    P, I = ctypes.c_void_p, ctypes.c_int
+    for name, args, res in (
+            ("sc_server_create", [ctypes.c_size_t, I, I, P], I),
+            ("sc_server_submit", [P, P, I, I, I, I, I, P, P], I),
+            ("sc_server_poll", [P, ctypes.c_int64, P], I),
+            ("sc_server_drain", [P, ctypes.c_double], I),
+            ("sc_server_stats", [P, P], I),
+            ("sc_server_destroy", [P], I)):
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+
+
+class Server:
+    """sc_server: continuous-batching request loop with a device-memory budget.
+
+    submit() takes a host image (numpy uint8 H x W x C) and returns a ticket; the result lands in a
+    pinned host array owned by this object (result(ticket)). Inputs are copied into pinned memory
+    here so the server's device copies are asynchronous."""
+
+    def __init__(self, budget_bytes: int = 40 << 30, max_batch: int = 64, streams: int = 16):
+        self.torch = _torch()
+        lib = load()
+        _server_sigs(lib)
+        h = ctypes.c_void_p(0)
+        _raise(lib.sc_server_create(ctypes.c_size_t(budget_bytes), max_batch, streams, ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, img: np.ndarray, target_w: int, target_h: int) -> int:
+        torch = self.torch
+        a = np.ascontiguousarray(img, dtype=np.uint8)
+        if a.ndim == 2:
+            a = a[:, :, None]
+        H, W, C = a.shape
+        src = torch.from_numpy(a).pin_memory()
+        dst = torch.empty((target_h, target_w, C), dtype=torch.uint8).pin_memory()
+        t = ctypes.c_int64(0)
+        _raise(load().sc_server_submit(self._h, ctypes.c_void_p(src.data_ptr()), H, W, C, int(target_w),
+                                       int(target_h), ctypes.c_void_p(dst.data_ptr()), ctypes.byref(t)))
+        self._keep[t.value] = (src, dst)
+        return t.value
+
+    def poll(self, ticket: int):
+        lat = ctypes.c_double(0.0)
+        rc = load().sc_server_poll(self._h, ticket, ctypes.byref(lat))
+        if rc < 0:
+            _raise(rc)
+        return rc == 1, lat.value
+
+    def result(self, ticket: int) -> np.ndarray:
+        return self._keep[ticket][1].numpy()
+
+    def release(self, ticket: int):
+        self._keep.pop(ticket, None)
+
+    def drain(self, timeout_s: float = 600.0):
+        _raise(load().sc_server_drain(self._h, ctypes.c_double(timeout_s)))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _raise(load().sc_server_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sc_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -11,14 +11,14 @@
 
 #include "../../include/sc.h"
 #include "sc_batch_item.h"
+#include "sc_host.h"
 #include "sc_internal.cuh"
 
 namespace sc {
 
 static thread_local std::string g_last_error = "no error";
 
-static int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
-static int fail(int code, const char *fmt, ...) {
+int fail(int code, const char *fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -115,7 +115,7 @@ static std::map<std::pair<int, void *>, Workspace *> g_ws;
 // One error word per device for batched launches (plans may run on any stream); sc_check reads it.
 static std::mutex g_gerr_mu;
 static std::map<int, int *> g_gerr;
-static int *device_error_word() {
+int *device_error_word() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
   std::lock_guard<std::mutex> lk(g_gerr_mu);
@@ -165,6 +165,16 @@ static int ensure_carve_buffers(Workspace &ws, int H, int W) {
   return SC_OK;
 }
 
+// Grow a stream's workspace for images up to H x W in both orientations (no allocation later).
+int workspace_reserve(cudaStream_t st, int H, int W) {
+  Workspace *wsp;
+  int rc = get_ws((void *)st, &wsp);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(wsp->mu);
+  if ((rc = ensure_flags(*wsp, st))) return rc;
+  return ensure_carve_buffers(*wsp, H, W);
+}
+
 static int launch_search(Workspace &ws, uint16_t *Ebase, int pe, int H, int W, int32_t *seam, int32_t *seam_log,
                          int64_t *cost, const int *gate, cudaStream_t st) {
   DpArgs a;
@@ -197,7 +207,7 @@ static int carve_pass_plain(Workspace &ws, uint32_t *img, int pitch, int H, int 
   return SC_OK;
 }
 
-static int check_carve_args(const void *img, int H, int W, int C, int tw, int th, const void *out) {
+int check_carve_args(const void *img, int H, int W, int C, int tw, int th, const void *out) {
   if (!img || !out) return fail(SC_EINVAL, "null image or output pointer");
   if (H < 1 || W < 1) return fail(SC_EINVAL, "H and W must be >= 1 (got %d x %d)", H, W);
   if (!valid_c(C)) return fail(SC_EINVAL, "C must be 1, 3 or 4 (got %d)", C);
@@ -209,8 +219,8 @@ static int check_carve_args(const void *img, int H, int W, int C, int tw, int th
   return SC_OK;
 }
 
-static int carve_impl(const uint8_t *img, int H, int W, int C, int tw, int th, uint8_t *out, int32_t *seam_log,
-                      int64_t *cost_log, cudaStream_t st) {
+int carve_impl(const uint8_t *img, int H, int W, int C, int tw, int th, uint8_t *out, int32_t *seam_log,
+               int64_t *cost_log, cudaStream_t st) {
   Workspace *wsp;
   int rc = get_ws((void *)st, &wsp);
   if (rc) return rc;
@@ -404,27 +414,16 @@ int sc_carve_host(const uint8_t *img_host, int H, int W, int C, int target_w, in
 namespace sc {
 
 // ---- batched carve (one persistent launch; images wider than a CTA go to the cluster path) ----
-struct BatchCfg {
-  int nw, kt;
-};
 static const BatchCfg kBatchCfgs[] = {{15, 16}, {15, 8}, {8, 16}, {8, 8}, {8, 32}};
 
-static int batch_need_width(const sc_image_desc &d) {
+int batch_need_width(const sc_image_desc &d) {
   const int nh = d.H - d.target_h;
   return nh > 0 ? (d.W > d.H ? d.W : d.H) : d.W;
 }
 
-struct BatchSetup {
-  std::vector<BatchItem> items;   // batched images (device pointers filled in)
-  std::vector<int> fallback;      // descriptor indices carved by the cluster path
-  size_t pool_bytes = 0;
-  int Smax = 1;
-};
-
-static size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Lays out every batched image's scratch in one pool (offsets; `pool` may be null to size it).
-static void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned char *pool, BatchSetup &b) {
+void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned char *pool, BatchSetup &b) {
   b.items.clear();
   b.fallback.clear();
   b.Smax = 1;

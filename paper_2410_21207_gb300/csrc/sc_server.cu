@@ -1,0 +1,443 @@
+// Serving form: a request loop with continuous batching and device-memory admission.
+//
+// Callers submit carve requests (host buffers) at any time. A worker thread repeatedly
+//   1. retires launch groups whose completion event has fired (frees their memory, time-stamps
+//      their requests),
+//   2. admits queued requests in arrival order while the device-memory ledger (one arena of the
+//      configured budget, first-fit) has room: requests that fit one CTA are gathered into a
+//      micro-batch (up to max_batch images) carved by one persistent k_batch launch; wider ones are
+//      carved alone by the cluster path,
+//   3. enqueues each group on a free stream: host->device copies, the carve, device->host copies,
+//      a completion event.
+// Groups on different streams run concurrently on the GPU, so requests that arrive while others
+// are being carved start as soon as memory and a stream are free, and their work overlaps.
+// Results do not depend on the grouping: every image is carved by the same integer arithmetic.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "sc_host.h"
+#include "sc_internal.cuh"
+
+namespace sc {
+
+int workspace_reserve(cudaStream_t st, int H, int W);   // sc_api.cu
+
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// first-fit sub-allocator over one device region (256-byte granules)
+struct Arena {
+  unsigned char *base = nullptr;
+  size_t size = 0, in_use = 0, peak = 0;
+  std::map<size_t, size_t> free_;   // offset -> bytes
+  bool init(size_t bytes) {
+    size = a256(bytes);
+    if (cudaMalloc(&base, size) != cudaSuccess) return false;
+    free_[0] = size;
+    return true;
+  }
+  bool alloc(size_t n, size_t *off) {
+    n = a256(n ? n : 1);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        *off = it->first;
+        const size_t rest = it->second - n;
+        const size_t o = it->first + n;
+        free_.erase(it);
+        if (rest) free_[o] = rest;
+        in_use += n;
+        peak = std::max(peak, in_use);
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    n = a256(n ? n : 1);
+    in_use -= n;
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+struct Request {
+  const uint8_t *in = nullptr;
+  uint8_t *out = nullptr;
+  int H = 0, W = 0, C = 0, tw = 0, th = 0;
+  double t_submit = 0, t_done = -1;
+  int status = 0;   // 0 queued, 1 on the GPU, 2 done, < 0 error
+};
+
+struct Group {
+  bool wide = false;                               // a single request on the cluster path
+  std::vector<int64_t> tickets;
+  std::vector<std::pair<size_t, size_t>> allocs;   // arena (offset, bytes)
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  int *h_err = nullptr;                            // pinned copy of the group's device error word
+};
+
+}  // namespace
+
+}  // namespace sc
+
+struct sc_server {
+  size_t budget = 0;
+  int max_batch = 64;
+  int dev = 0;
+  sc::BatchCfg cfg{15, 16};
+  int sms = 1, occ = 1;
+  sc::Arena arena;
+  std::vector<cudaStream_t> batch_streams, big_streams;   // free pools
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<int64_t> queue;
+  std::unordered_map<int64_t, sc::Request> reqs;
+  std::vector<sc::Group> inflight;
+  std::vector<double> latencies;
+  int64_t next_ticket = 1;
+  int64_t done_count = 0, batched_count = 0, big_count = 0, groups = 0;
+  bool stop = false;
+  int device_errors = 0;
+  std::thread worker;
+};
+
+namespace sc {
+namespace {
+
+size_t item_bytes(const sc_image_desc &d, const BatchCfg &c, int *Smax) {
+  BatchSetup b;
+  batch_layout(&d, 1, c, nullptr, b);
+  if (!b.items.empty()) *Smax = std::max(*Smax, b.Smax);
+  return b.pool_bytes;
+}
+
+bool fits_cta(const sc_server *s, const Request &r) {
+  sc_image_desc d{};
+  d.H = r.H; d.W = r.W; d.C = r.C; d.target_w = r.tw; d.target_h = r.th;
+  return batch_need_width(d) <= batch_width_limit(s->cfg.nw, s->cfg.kt);
+}
+
+// Retire finished groups (caller holds the lock).
+void retire(sc_server *s) {
+  const double t = now_s();
+  for (size_t g = 0; g < s->inflight.size();) {
+    Group &G = s->inflight[g];
+    const cudaError_t q = cudaEventQuery(G.done);
+    if (q == cudaErrorNotReady) { ++g; continue; }
+    const bool ok = (q == cudaSuccess) && (*G.h_err == 0);
+    if (!ok) s->device_errors++;
+    for (int64_t tk : G.tickets) {
+      Request &r = s->reqs[tk];
+      r.t_done = t;
+      r.status = ok ? 2 : SC_EINTERNAL;
+      s->latencies.push_back(t - r.t_submit);
+      s->done_count++;
+    }
+    for (auto &a : G.allocs) s->arena.release(a.first, a.second);
+    cudaEventDestroy(G.done);
+    cudaFreeHost(G.h_err);
+    if (G.wide)
+      s->big_streams.push_back(G.stream);
+    else
+      s->batch_streams.push_back(G.stream);
+    s->inflight.erase(s->inflight.begin() + g);
+  }
+  s->cv.notify_all();
+}
+
+// Start one group if possible (caller holds the lock). Returns true if something was launched.
+bool admit(sc_server *s) {
+  if (s->queue.empty()) return false;
+  const int64_t head = s->queue.front();
+  Request &r0 = s->reqs[head];
+  if (!fits_cta(s, r0)) {
+    // a request wider than one CTA: alone, on the cluster path (its scratch is the stream's
+    // workspace, reserved at creation)
+    if (s->big_streams.empty()) return false;
+    const size_t nin = (size_t)r0.H * r0.W * r0.C, nout = (size_t)r0.th * r0.tw * r0.C;
+    size_t oin, oout, oerr;
+    if (!s->arena.alloc(nin, &oin)) return false;
+    if (!s->arena.alloc(nout, &oout)) { s->arena.release(oin, nin); return false; }
+    if (!s->arena.alloc(4, &oerr)) { s->arena.release(oin, nin); s->arena.release(oout, nout); return false; }
+    Group G;
+    G.wide = true;
+    G.stream = s->big_streams.back();
+    s->big_streams.pop_back();
+    G.tickets.push_back(head);
+    G.allocs = {{oin, nin}, {oout, nout}, {oerr, 4}};
+    cudaHostAlloc((void **)&G.h_err, sizeof(int), cudaHostAllocDefault);
+    *G.h_err = 0;
+    uint8_t *din = s->arena.base + oin, *dout = s->arena.base + oout;
+    cudaMemcpyAsync(din, r0.in, nin, cudaMemcpyHostToDevice, G.stream);
+    const int rc = carve_impl(din, r0.H, r0.W, r0.C, r0.tw, r0.th, dout, nullptr, nullptr, G.stream);
+    *G.h_err = rc ? 1 : 0;
+    cudaMemcpyAsync(r0.out, dout, nout, cudaMemcpyDeviceToHost, G.stream);
+    cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming);
+    cudaEventRecord(G.done, G.stream);
+    r0.status = 1;
+    s->queue.pop_front();
+    s->inflight.push_back(G);
+    s->big_count++;
+    s->groups++;
+    return true;
+  }
+  // a micro-batch of the queued requests that fit one CTA, in arrival order
+  if (s->batch_streams.empty()) return false;
+  std::vector<int64_t> take;
+  std::vector<sc_image_desc> descs;
+  std::vector<std::pair<size_t, size_t>> allocs;
+  int Smax = 1;
+  for (int64_t tk : s->queue) {
+    if ((int)take.size() >= s->max_batch) break;
+    Request &r = s->reqs[tk];
+    if (!fits_cta(s, r)) break;   // keep arrival order: a wide request waits for its own turn
+    sc_image_desc d{};
+    d.H = r.H; d.W = r.W; d.C = r.C; d.target_w = r.tw; d.target_h = r.th;
+    int sm = Smax;
+    const size_t scratch = item_bytes(d, s->cfg, &sm);
+    if (batch_smem_bytes(s->cfg.nw, s->cfg.kt, sm) > 232448 - 64) break;
+    const size_t nin = (size_t)r.H * r.W * r.C, nout = (size_t)r.th * r.tw * r.C;
+    size_t oin, oout, osc;
+    if (!s->arena.alloc(nin, &oin)) break;
+    if (!s->arena.alloc(nout, &oout)) { s->arena.release(oin, nin); break; }
+    if (!s->arena.alloc(scratch, &osc)) { s->arena.release(oin, nin); s->arena.release(oout, nout); break; }
+    allocs.push_back({oin, nin});
+    allocs.push_back({oout, nout});
+    allocs.push_back({osc, scratch});
+    d.img = s->arena.base + oin;
+    d.out = s->arena.base + oout;
+    d.seam_log = nullptr;
+    descs.push_back(d);
+    take.push_back(tk);
+    Smax = sm;
+  }
+  if (take.empty()) {
+    for (auto &a : allocs) s->arena.release(a.first, a.second);
+    return false;
+  }
+  const int n = (int)take.size();
+  size_t otab, oq;
+  const size_t tab_bytes = (size_t)n * sizeof(BatchItem);
+  if (!s->arena.alloc(tab_bytes, &otab) || !s->arena.alloc(256, &oq)) {
+    for (auto &a : allocs) s->arena.release(a.first, a.second);
+    return false;
+  }
+  allocs.push_back({otab, tab_bytes});
+  allocs.push_back({oq, 256});
+  // per-image scratch layouts, each placed in its own arena block
+  std::vector<BatchItem> items(n);
+  for (int k = 0; k < n; ++k) {
+    BatchSetup b;
+    batch_layout(&descs[k], 1, s->cfg, s->arena.base + allocs[3 * k + 2].first, b);
+    items[k] = b.items[0];
+  }
+  Group G;
+  G.stream = s->batch_streams.back();
+  s->batch_streams.pop_back();
+  G.tickets = take;
+  G.allocs = allocs;
+  cudaHostAlloc((void **)&G.h_err, sizeof(int), cudaHostAllocDefault);
+  *G.h_err = 0;
+  int *q = reinterpret_cast<int *>(s->arena.base + oq);
+  int *derr = q + 1;
+  BatchItem *dtab = reinterpret_cast<BatchItem *>(s->arena.base + otab);
+  cudaMemcpyAsync(dtab, items.data(), tab_bytes, cudaMemcpyHostToDevice, G.stream);   // pageable: staged
+  cudaMemsetAsync(q, 0, 2 * sizeof(int), G.stream);
+  for (int k = 0; k < n; ++k) {
+    Request &r = s->reqs[take[k]];
+    cudaMemcpyAsync((void *)descs[k].img, r.in, (size_t)r.H * r.W * r.C, cudaMemcpyHostToDevice, G.stream);
+    r.status = 1;
+  }
+  int grid = s->sms * s->occ;
+  if (grid > n) grid = n;
+  const cudaError_t le = launch_batch(s->cfg.nw, s->cfg.kt, dtab, n, Smax, grid, q, derr, G.stream);
+  if (le != cudaSuccess) *G.h_err = 1;
+  for (int k = 0; k < n; ++k) {
+    Request &r = s->reqs[take[k]];
+    cudaMemcpyAsync(r.out, descs[k].out, (size_t)r.th * r.tw * r.C, cudaMemcpyDeviceToHost, G.stream);
+  }
+  cudaMemcpyAsync(G.h_err, derr, sizeof(int), cudaMemcpyDeviceToHost, G.stream);
+  cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming);
+  cudaEventRecord(G.done, G.stream);
+  for (int k = 0; k < n; ++k) s->queue.pop_front();
+  s->inflight.push_back(G);
+  s->batched_count += n;
+  s->groups++;
+  return true;
+}
+
+void worker_loop(sc_server *s) {
+  cudaSetDevice(s->dev);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    retire(s);
+    bool launched = false;
+    while (admit(s)) launched = true;
+    if (s->stop && s->queue.empty() && s->inflight.empty()) break;
+    if (!launched) {
+      // nothing to start: wait briefly for a submission or a completion
+      s->cv.wait_for(lk, std::chrono::microseconds(s->inflight.empty() ? 500 : 20));
+    }
+  }
+}
+
+}  // namespace
+}  // namespace sc
+
+using namespace sc;
+
+extern "C" {
+
+int sc_server_create(size_t budget_bytes, int max_batch, int streams, sc_server **out) {
+  if (!out) return fail(SC_EINVAL, "null server pointer");
+  *out = nullptr;
+  if (budget_bytes < ((size_t)64 << 20)) return fail(SC_EINVAL, "budget must be at least 64 MiB");
+  if (max_batch < 1 || streams < 2) return fail(SC_EINVAL, "max_batch >= 1 and streams >= 2 required");
+  sc_server *s = new sc_server();
+  s->budget = budget_bytes;
+  s->max_batch = max_batch;
+  if (cudaGetDevice(&s->dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->dev) != cudaSuccess) {
+    delete s;
+    return fail(SC_ECUDA, "no CUDA device");
+  }
+  if (!s->arena.init(budget_bytes)) {
+    delete s;
+    return fail(SC_ENOMEM, "cannot allocate the %zu-byte device arena", budget_bytes);
+  }
+  s->occ = batch_blocks_per_sm(s->cfg.nw, s->cfg.kt, 1);
+  for (int k = 0; k < streams; ++k) {
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete s;
+      return fail(SC_ECUDA, "stream creation failed");
+    }
+    // half the streams carve micro-batches, half carve wide requests on the cluster path
+    if (k % 2 == 0) {
+      s->batch_streams.push_back(st);
+    } else {
+      const int rc = workspace_reserve(st, 4096, 4096);   // no allocation while serving
+      if (rc) {
+        delete s;
+        return rc;
+      }
+      s->big_streams.push_back(st);
+    }
+  }
+  s->worker = std::thread(worker_loop, s);
+  *out = s;
+  return SC_OK;
+}
+
+int sc_server_submit(sc_server *s, const uint8_t *img_host, int H, int W, int C, int target_w, int target_h,
+                     uint8_t *out_host, int64_t *ticket) {
+  if (!s || !ticket) return fail(SC_EINVAL, "null server or ticket pointer");
+  int rc = check_carve_args(img_host, H, W, C, target_w, target_h, out_host);
+  if (rc) return rc;
+  if (H > 4096 || W > 4096) return fail(SC_EINVAL, "served images are limited to 4096 x 4096");
+  Request r;
+  r.in = img_host;
+  r.out = out_host;
+  r.H = H; r.W = W; r.C = C; r.tw = target_w; r.th = target_h;
+  r.t_submit = now_s();
+  size_t need = (size_t)H * W * C + (size_t)target_h * target_w * C + 1024;
+  if (fits_cta(s, r)) {
+    sc_image_desc d{};
+    d.H = H; d.W = W; d.C = C; d.target_w = target_w; d.target_h = target_h;
+    int sm = 1;
+    need += item_bytes(d, s->cfg, &sm) + 4096;
+  }
+  if (need > s->arena.size) return fail(SC_ENOMEM, "a %d x %d request needs more than the whole budget", W, H);
+  std::lock_guard<std::mutex> lk(s->mu);
+  const int64_t t = s->next_ticket++;
+  s->reqs[t] = r;
+  s->queue.push_back(t);
+  *ticket = t;
+  s->cv.notify_all();
+  return SC_OK;
+}
+
+int sc_server_poll(sc_server *s, int64_t ticket, double *latency_s) {
+  if (!s) return fail(SC_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return fail(SC_EINVAL, "unknown ticket");
+  if (it->second.status == 2) {
+    if (latency_s) *latency_s = it->second.t_done - it->second.t_submit;
+    return 1;
+  }
+  if (it->second.status < 0) return it->second.status;
+  return 0;
+}
+
+int sc_server_drain(sc_server *s, double timeout_s) {
+  if (!s) return fail(SC_EINVAL, "null server");
+  std::unique_lock<std::mutex> lk(s->mu);
+  const double t_end = now_s() + timeout_s;
+  while (!(s->queue.empty() && s->inflight.empty())) {
+    if (now_s() > t_end) return fail(SC_ETIMEOUT, "requests still pending after %.1f s", timeout_s);
+    s->cv.wait_for(lk, std::chrono::milliseconds(1));
+  }
+  return s->device_errors ? fail(SC_EINTERNAL, "%d launch groups reported device errors", s->device_errors) : SC_OK;
+}
+
+int sc_server_stats(sc_server *s, sc_server_stats_t *out) {
+  if (!s || !out) return fail(SC_EINVAL, "null pointer");
+  std::lock_guard<std::mutex> lk(s->mu);
+  out->completed = s->done_count;
+  out->queued = (int64_t)s->queue.size();
+  out->in_flight_groups = (int64_t)s->inflight.size();
+  out->groups = s->groups;
+  out->batched = s->batched_count;
+  out->cluster_path = s->big_count;
+  out->bytes_in_use = s->arena.in_use;
+  out->peak_bytes = s->arena.peak;
+  out->budget_bytes = s->arena.size;
+  out->device_errors = s->device_errors;
+  std::vector<double> l = s->latencies;
+  std::sort(l.begin(), l.end());
+  auto pct = [&](double p) { return l.empty() ? 0.0 : l[(size_t)std::min<double>(l.size() - 1, p * (l.size() - 1) + 0.5)]; };
+  out->p50_s = pct(0.50);
+  out->p99_s = pct(0.99);
+  out->max_s = l.empty() ? 0.0 : l.back();
+  return SC_OK;
+}
+
+int sc_server_destroy(sc_server *s) {
+  if (!s) return SC_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv.notify_all();
+  }
+  if (s->worker.joinable()) s->worker.join();
+  for (cudaStream_t st : s->batch_streams) cudaStreamDestroy(st);
+  for (cudaStream_t st : s->big_streams) cudaStreamDestroy(st);
+  if (s->arena.base) cudaFree(s->arena.base);
+  delete s;
+  return SC_OK;
+}
+
+}  // extern "C"
