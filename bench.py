@@ -40,6 +40,9 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (256-image) measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving (Poisson trace) measurement")
+    ap.add_argument("--no-4k", action="store_true", help="skip the 3840x2160 measurement")
+    ap.add_argument("--serving-requests", type=int, default=300)
     ap.add_argument("--profile-search", metavar="HxW", default=None,
                     help="only call sc_find_seam a few times on a seeded HxW energy map (for ncu captures)")
     return ap.parse_args()
@@ -198,6 +201,103 @@ def batched_measurement(sc, torch, dev, flush, steps):
             "batched_over_plain": batched_sps / plain_sps}
 
 
+def _gen_request(args):
+    """Worker (spawned process): pixels of request k of the serving trace."""
+    import sys as _sys
+    _sys.path.insert(0, ROOT)
+    from paper_2410_21207_gb300 import synth
+    k, n = args
+    return k, synth.config5(n=n)[k].make()
+
+
+def pregenerate_serving(n):
+    """Images of the first n requests of the serving trace, made by a spawned process pool before
+    any GPU work in this process."""
+    from multiprocessing import get_context
+    procs = max(1, min(14, (os.cpu_count() or 2) - 2))
+    with get_context("spawn").Pool(procs) as pool:
+        return dict(pool.map(_gen_request, [(k, n) for k in range(n)], chunksize=4))
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(q * (len(xs) - 1) + 0.5))] if xs else None
+
+
+def serving_measurement(sc, torch, dev, imgs, n):
+    """Config 5's first n requests (Poisson arrivals at 200/s, sizes log-uniform 128..4096 x
+    128..2160) replayed in real time into sc_server (40 GB budget), against the plain path: the same
+    arrivals served first-come first-served, one request at a time, by sc_carve_plain (device image
+    in, device image out; the served path also copies host->device->host)."""
+    from paper_2410_21207_gb300 import synth
+    reqs = synth.config5(n=n)
+    seams = sum(r.seams for r in reqs)
+    srv = sc.Server(budget_bytes=40 << 30, max_batch=64, streams=16)
+    w = srv.submit(imgs[0], reqs[0].target_w, reqs[0].target_h)
+    srv.drain()
+    srv.release(w)
+    tickets = []
+    t0 = time.perf_counter()
+    for k, r in enumerate(reqs):
+        delay = r.arrival_s - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(imgs[k], r.target_w, r.target_h))
+    srv.drain(900)
+    wall = time.perf_counter() - t0
+    lats = [srv.poll(t)[1] for t in tickets]
+    st = srv.stats()
+    srv.close()
+    # plain path: FIFO, one request at a time, per-seam launches
+    dimgs = [torch.from_numpy(imgs[k]).to(dev) for k in range(n)]
+    sc.carve(dimgs[0], reqs[0].target_w, reqs[0].target_h, plain=True)
+    torch.cuda.synchronize(dev)
+    plain_lat, clock = [], 0.0
+    tp0 = time.perf_counter()
+    for k, r in enumerate(reqs):
+        start = max(clock, r.arrival_s)
+        t1 = time.perf_counter()
+        sc.carve(dimgs[k], r.target_w, r.target_h, plain=True)
+        torch.cuda.synchronize(dev)
+        clock = start + (time.perf_counter() - t1)
+        plain_lat.append(clock - r.arrival_s)
+    plain_busy = time.perf_counter() - tp0
+    sc.check()
+    return {"workload": f"first {n} requests of the 10,000-request trace (seed 5): Poisson 200 req/s, "
+                        "W, H log-uniform 128..4096 x 128..2160, target 50..90 % x 80..100 %",
+            "served": {"req_per_s": n / wall, "seams_per_s": seams / wall, "p50_ms": 1e3 * _pct(lats, 0.5),
+                       "p99_ms": 1e3 * _pct(lats, 0.99), "launch_groups": st["groups"],
+                       "batched": st["batched"] - 1, "cluster_path": st["cluster_path"],
+                       "peak_device_bytes": st["peak_bytes"], "budget_bytes": st["budget_bytes"]},
+            "plain": {"req_per_s": n / plain_busy, "seams_per_s": seams / plain_busy,
+                      "p50_ms": 1e3 * _pct(plain_lat, 0.5), "p99_ms": 1e3 * _pct(plain_lat, 0.99),
+                      "note": "same arrivals, first-come first-served, one request at a time"},
+            "served_over_plain_throughput": (seams / wall) / (seams / plain_busy)}
+
+
+def fourk_measurement(sc, torch, dev, flush, steps):
+    """Config 3: 3840x2160 -> 2880x1620 (960 vertical + 540 horizontal seams via transposition)."""
+    from paper_2410_21207_gb300 import synth
+    job = synth.config3()
+    img = torch.from_numpy(job.make()).to(dev)
+    sc.carve(img, job.target_w, job.target_h)
+    torch.cuda.synchronize(dev)
+    ms = []
+    for _ in range(max(1, min(2, steps))):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sc.carve(img, job.target_w, job.target_h)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    sc.check()
+    t = statistics.median(ms) / 1000.0
+    return {"workload": job.name, "seams_per_s": job.seams / t, "mpix_seam_per_s": job.mpix_seams() / t,
+            "ms_per_carve": 1e3 * t}
+
+
 def profile_search(spec: str):
     """sc_find_seam four times on a seeded H x W uint16 energy map (the kernel to capture is k_dp)."""
     import numpy as np
@@ -256,6 +356,9 @@ def run_native(a):
     from paper_2410_21207_gb300 import binding as sc
 
     ws, rank, local = _dist()
+    serving_imgs = None
+    if rank == 0 and not a.no_serving:
+        serving_imgs = pregenerate_serving(a.serving_requests)   # before any GPU work (spawned pool)
     if ws > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -355,6 +458,10 @@ def run_native(a):
                        "d2h_bytes_per_step": th * tw * 3}
     if rank == 0 and not a.no_batched:
         line["batched"] = batched_measurement(sc, torch, dev, flush, a.steps)
+    if rank == 0 and not a.no_4k:
+        line["uhd_3840x2160"] = fourk_measurement(sc, torch, dev, flush, a.steps)
+    if rank == 0 and serving_imgs is not None:
+        line["serving"] = serving_measurement(sc, torch, dev, serving_imgs, a.serving_requests)
     if rank == 0 and not a.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(job, img_np)
     if rank == 0:

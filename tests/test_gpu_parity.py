@@ -147,3 +147,24 @@ def test_invalid_arguments_raise(dev):
         sc.carve(img, 11, 10)
     with pytest.raises(sc.ScError):
         sc.carve(img, 0, 10)
+
+
+@pytest.mark.slow
+def test_carve_config3_full(dev):
+    """3840x2160 -> 2880x1620: 960 vertical then 540 horizontal seams (through the transpose), every
+    seam index, cost and output byte. The oracle (about a minute of CPU) runs in a thread while the
+    GPU carves."""
+    import threading
+    job = synth.config3()
+    img = job.make()
+    ref = {}
+    th = threading.Thread(target=lambda: ref.update(r=oracle.carve(img, job.target_w, job.target_h, with_log=True)))
+    th.start()
+    out, log, cost = sc.carve(_to_dev(img, dev), job.target_w, job.target_h, with_log=True)
+    sc.check()
+    out, log, cost = _np(out), _np(log), _np(cost)
+    th.join()
+    r_out, r_log, r_cost = ref["r"]
+    np.testing.assert_array_equal(log, r_log)
+    np.testing.assert_array_equal(cost, r_cost)
+    np.testing.assert_array_equal(out, r_out)
