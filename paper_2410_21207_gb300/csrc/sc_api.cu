@@ -13,6 +13,7 @@
 #include "sc_batch_item.h"
 #include "sc_host.h"
 #include "sc_internal.cuh"
+#include "sc_rowops.cuh"
 
 namespace sc {
 
@@ -99,12 +100,13 @@ struct Workspace {
   DevBuf<uint32_t> img, img2, Mrow, patch;
   DevBuf<uint16_t> E;
   DevBuf<int32_t> seam;
+  DevBuf<int16_t> lists;          // two generations of pending-removal lists
   DevBuf<uint8_t> hin, hout;     // staging for the host-pointer entry point
   DevBuf<int> flags;             // [0] error word, [1] energy-range gate
   bool flags_zeroed = false;
   void release_all() {
     img.release(); img2.release(); Mrow.release(); patch.release();
-    E.release(); seam.release(); hin.release(); hout.release(); flags.release();
+    E.release(); seam.release(); lists.release(); hin.release(); hout.release(); flags.release();
     flags_zeroed = false;
   }
 };
@@ -162,6 +164,7 @@ static int ensure_carve_buffers(Workspace &ws, int H, int W) {
   SC_CUDA(ws.Mrow.ensure((size_t)(S + 1) * pe));
   SC_CUDA(ws.seam.ensure((size_t)R));
   SC_CUDA(ws.patch.ensure((size_t)R));
+  SC_CUDA(ws.lists.ensure((size_t)2 * R * RPEND));
   return SC_OK;
 }
 
@@ -192,18 +195,38 @@ static int launch_search(Workspace &ws, uint16_t *Ebase, int pe, int H, int W, i
   return SC_OK;
 }
 
-// (count) vertical seams of an H x W word image in place; E holds its energy (pitch pe).
+// (count) vertical seams of an H x W word image; ws.E holds its energy (pitch pe). Per seam: the
+// search, then one warp per row computes the refreshed energy pair through the pending-removal
+// lists, adds the removal to the row's list and compacts the energy row. The image words are
+// compacted every RPEND seams and at the end of the pass.
 static int carve_pass_plain(Workspace &ws, uint32_t *img, int pitch, int H, int W, int count, int pe,
                             int32_t *seam_log, int64_t *cost_log, cudaStream_t st) {
-  uint16_t *E = ws.E.p;
+  int16_t *lb[2] = {ws.lists.p, ws.lists.p + (size_t)H * RPEND};
+  int cur = 0, m = 0;
   for (int t = 0; t < count; ++t) {
     const int w = W - t;
-    int rc = launch_search(ws, E, pe, H, w, ws.seam.p, seam_log ? seam_log + (size_t)t * H : nullptr,
-                           cost_log ? cost_log + t : nullptr, nullptr, st);
-    if (rc) return rc;
-    SC_CUDA(timed("patch", st, [&] { return launch_patch(img, pitch, H, w, ws.seam.p, ws.patch.p, ws.flags.p, st); }));
-    SC_CUDA(timed("shift", st, [&] { return launch_shift(img, pitch, E + E_PADL, pe, H, w, ws.seam.p, ws.patch.p, st); }));
+    DpArgs a;
+    a.E = ws.E.p + E_PADL;
+    a.pitch_e = pe;
+    a.H = H;
+    a.W = w;
+    a.Mrow = ws.Mrow.p + E_PADL;
+    a.seam = ws.seam.p;
+    a.seam_log = seam_log ? seam_log + (size_t)t * H : nullptr;
+    a.cost = cost_log ? cost_log + t : nullptr;
+    a.err = ws.flags.p;
+    a.gate = nullptr;
+    SC_CUDA(timed("dp", st, [&] { return launch_dp(a, st); }));
+    SC_CUDA(timed("refresh", st, [&] {
+      return launch_refresh(img, pitch, ws.E.p + E_PADL, pe, H, w, ws.seam.p, lb[cur], lb[cur ^ 1], m, ws.flags.p, st);
+    }));
+    cur ^= 1;
+    if (++m == RPEND) {
+      SC_CUDA(timed("compact", st, [&] { return launch_compact_lazy(img, pitch, H, w - 1, lb[cur], m, st); }));
+      m = 0;
+    }
   }
+  if (m > 0) SC_CUDA(timed("compact", st, [&] { return launch_compact_lazy(img, pitch, H, W - count, lb[cur], m, st); }));
   return SC_OK;
 }
 
@@ -414,7 +437,7 @@ int sc_carve_host(const uint8_t *img_host, int H, int W, int C, int target_w, in
 namespace sc {
 
 // ---- batched carve (one persistent launch; images wider than a CTA go to the cluster path) ----
-static const BatchCfg kBatchCfgs[] = {{15, 16}, {15, 8}, {8, 16}, {8, 8}, {8, 32}};
+static const BatchCfg kBatchCfgs[] = {{15, 16}, {15, 8}, {12, 8}, {12, 16}, {8, 16}, {8, 8}, {8, 32}};
 
 int batch_need_width(const sc_image_desc &d) {
   const int nh = d.H - d.target_h;
@@ -431,7 +454,11 @@ void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned
   const int limit = batch_width_limit(c.nw, c.kt);
   for (int k = 0; k < n; ++k) {
     const sc_image_desc &d = descs[k];
-    if (batch_need_width(d) > limit) {
+    const int nh0 = d.H - d.target_h;
+    const int rows0 = (nh0 > 0 && d.target_w > d.H) ? d.target_w : d.H;
+    // the refreshed pairs of a pass live in the CTA's staging ring between searches
+    const size_t ring_bytes = (size_t)3 * c.kt * (c.nw * (128 - 2 * c.kt) + 2 * c.kt) * 2;
+    if (batch_need_width(d) > limit || (size_t)rows0 * 4 > ring_bytes) {
       b.fallback.push_back(k);
       continue;
     }
@@ -457,7 +484,7 @@ void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned
     it.E = (uint16_t *)take((size_t)rows_max * it.pe * 2);
     it.Mrow = (uint32_t *)take((size_t)(S + 1) * it.pe * 4);
     it.seam = (int32_t *)take((size_t)rows_max * 4);
-    it.patch = (uint32_t *)take((size_t)rows_max * 4);
+    it.lists = (int16_t *)take((size_t)2 * rows_max * RPEND * 2);
     b.items.push_back(it);
   }
   b.pool_bytes = off;
@@ -480,7 +507,7 @@ static BatchCfg default_batch_cfg(const sc_image_desc *descs, int n) {
   for (const BatchCfg &c : kBatchCfgs) {
     BatchSetup b;
     batch_layout(descs, n, c, nullptr, b);
-    if (batch_smem_bytes(c.nw, c.kt, b.Smax) > 232448 - 64) continue;
+    if (batch_smem_bytes(c.nw, c.kt, b.Smax) > 232448 - 1024) continue;
     const int cover = (int)b.items.size();
     if (cover > best_cover) { best_cover = cover; best = c; }
   }
@@ -590,7 +617,7 @@ int sc_batch_plan_create(const sc_image_desc *descs, int n, int autotune, void *
       BatchSetup b;
       batch_layout(descs, n, c, nullptr, b);
       if (b.items.size() < b0.items.size()) continue;
-      if (batch_smem_bytes(c.nw, c.kt, b.Smax) > 232448 - 64) continue;
+      if (batch_smem_bytes(c.nw, c.kt, b.Smax) > 232448 - 1024) continue;
       BatchRun trial;
       if ((rc = batch_prepare(trial, descs, n, c))) { delete p; return rc; }
       BatchSetup keep = trial.setup;

@@ -36,12 +36,19 @@ __device__ inline void cta_transpose(const uint32_t *src, int ps, int rows, int 
   }
 }
 
+// (count) vertical seams of a rows x cols word image, whose energy is in it.E. Per seam: the
+// search, then one warp per row computes the refreshed energy pair through the pending-removal
+// lists, adds the removal to the row's list and compacts the energy row; the words are compacted
+// every RPEND seams and at the end of the pass.
 template <int NW, int KT>
 __device__ void batch_seam_pass(const BatchItem &it, uint32_t *words, int rows, int cols, int count,
                                 int32_t *log, int64_t *costs, unsigned char *smem, int Smax, SearchState &st,
                                 int *err) {
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  int16_t *lb[2] = {it.lists, it.lists + (size_t)rows * RPEND};
+  // the staging ring is idle between searches: it holds the rows' refreshed pairs
+  uint32_t *pairs = reinterpret_cast<uint32_t *>(smem + search_plan<NW, KT, false>(Smax).ring);
+  int cur = 0, m = 0;
   for (int t = 0; t < count; ++t) {
     const int w = cols - t;
     SearchArgs a;
@@ -55,16 +62,40 @@ __device__ void batch_seam_pass(const BatchItem &it, uint32_t *words, int rows, 
     a.cost = costs ? costs + t : nullptr;
     a.err = err;
     a.gated = false;
-    seam_search<NW, KT, false>(a, smem, Smax, st);   // ends with a CTA barrier: seam[] is complete
+    seam_search<NW, KT, false>(a, smem, Smax, st);   // ends with a CTA barrier: the seam is complete
+    // every row's refreshed pair and list update, one thread per row (into the idle staging ring)
     bool bad = false;
-    for (int i = tid; i < rows; i += nthr) it.patch[i] = patch_row(words, it.pitch, rows, w, it.seam, i, &bad);
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      pairs[i] = patch_row_lazy(words, it.pitch, rows, w, it.seam, lb[cur], m, i, &bad);
+      if (!bad) list_insert(lb[cur] + (size_t)i * RPEND, lb[cur ^ 1] + (size_t)i * RPEND, m, it.seam[i]);
+    }
     if (bad) atomicOr(err, ERR_BAD_SEAM);
     __syncthreads();
+    // energy rows compacted past the seam, the pair at the new columns s-1 and s, one warp per row
     for (int i = warp; i < rows; i += nwarps) {
       const int s = it.seam[i];
-      if (s >= 0 && s < w) compact_row(words, it.pitch, it.E + E_PADL, it.pe, w, s, it.patch[i], i, lane);
+      if (s < 0 || s >= w) continue;
+      uint16_t *er = it.E + E_PADL + (size_t)i * it.pe;
+      shift_row(er, s, w, lane);
+      if (lane == 0) {
+        const uint32_t pr = pairs[i];
+        if (s >= 1) er[s - 1] = (uint16_t)(pr & 0xFFFFu);
+        if (s <= w - 2) er[s] = (uint16_t)(pr >> 16);
+      }
     }
-    fence_proxy_async_global();   // the next search stages the energy rows with TMA (async proxy)
+    cur ^= 1;
+    fence_proxy_async_global();   // the next search stages the compacted energy rows with TMA
+    __syncthreads();
+    if (++m == RPEND) {
+      for (int i = warp; i < rows; i += nwarps)
+        compact_row_lazy(words + (size_t)i * it.pitch, lb[cur] + (size_t)i * RPEND, m, w - 1, lane);
+      m = 0;
+      __syncthreads();
+    }
+  }
+  if (m > 0) {
+    for (int i = warp; i < rows; i += nwarps)
+      compact_row_lazy(words + (size_t)i * it.pitch, lb[cur] + (size_t)i * RPEND, m, cols - count, lane);
     __syncthreads();
   }
 }
@@ -119,20 +150,27 @@ __global__ void __launch_bounds__(Geo<NW, KT, false>::THREADS, 1)
     k_batch(const BatchItem *__restrict__ items, int n, int Smax, int *queue, int *err) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int next;
+  // the current image's descriptor lives in shared memory and its fields are read where they are
+  // used, so they do not occupy registers across the seam loop
+  __shared__ BatchItem cur;
   search_init<NW, KT, false>(smem, Smax);
   __syncthreads();
   SearchState st;
   for (;;) {
-    if (threadIdx.x == 0) next = atomicAdd(queue, 1);
+    if (threadIdx.x == 0) {
+      next = atomicAdd(queue, 1);
+      if (next < n) cur = items[next];
+    }
     __syncthreads();
     const int k = next;
     __syncthreads();
     if (k >= n) break;
-    batch_carve_item<NW, KT>(items[k], smem, Smax, st, err);
+    batch_carve_item<NW, KT>(cur, smem, Smax, st, err);
+    __syncthreads();
   }
 }
 
-constexpr size_t BATCH_SMEM_MAX = 232448 - 64;   // the opt-in limit minus the kernel's static shared memory
+constexpr size_t BATCH_SMEM_MAX = 232448 - 1024;   // the opt-in limit minus room for static shared memory
 
 template <int NW, int KT>
 cudaError_t batch_configure_cfg() {

@@ -16,10 +16,10 @@ struct BatchItem {
   int pad;
   uint32_t *img_w;      // max(H,W) x pitch words: the image being carved
   uint32_t *img2_w;     // max(H,W) x pitch words: its transpose for the horizontal pass
-  uint16_t *E;          // max(H,W) x pe energies (column 0 at E + E_PADL)
-  uint32_t *Mrow;       // (ceil(max(H,W)/KS) + 1) x pe saved cost rows (column 0 at Mrow + E_PADL)
-  int32_t *seam;        // max(H,W)
-  uint32_t *patch;      // max(H,W)
+  uint16_t *E;          // rows x pe energies (column 0 at E + E_PADL)
+  uint32_t *Mrow;       // (ceil(rows/KS) + 1) x pe saved cost rows (column 0 at Mrow + E_PADL)
+  int32_t *seam;        // rows
+  int16_t *lists;       // two generations of pending-removal lists, rows x RPEND each
 };
 
 // width a CTA of nw compute warps with tile height kt covers

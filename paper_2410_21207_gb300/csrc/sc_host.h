@@ -28,6 +28,7 @@ struct BatchSetup {
   int Smax = 1;
 };
 inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
 // widest searched width of an image (its width, or its height when it has horizontal seams)
 int batch_need_width(const sc_image_desc &d);
 void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned char *pool, BatchSetup &b);

@@ -72,5 +72,13 @@ cudaError_t launch_patch(const uint32_t *img, int pitch_img, int H, int W, const
 cudaError_t launch_shift(uint32_t *img, int pitch_img, uint16_t *E, int pitch_e, int H, int W, const int32_t *seam,
                          const uint32_t *patch, cudaStream_t st);
 cudaError_t launch_dp(const DpArgs &a, cudaStream_t st);
+// lazy image compaction (sc_rowops.cuh): refresh + list update per seam, bulk compaction
+cudaError_t launch_patch_lazy(const uint32_t *img, int pitch, int H, int W, const int32_t *seam,
+                              const int16_t *lists_in, int16_t *lists_out, int m, uint32_t *patch, int *err,
+                              cudaStream_t st);
+cudaError_t launch_compact_lazy(uint32_t *img, int pitch, int H, int w, const int16_t *lists, int m, cudaStream_t st);
+// per seam: refreshed pair through the lazy map, list update and energy compaction (one warp per row)
+cudaError_t launch_refresh(const uint32_t *img, int pitch, uint16_t *E, int pe, int H, int W, const int32_t *seam,
+                           const int16_t *lists_in, int16_t *lists_out, int m, int *err, cudaStream_t st);
 
 }  // namespace sc

@@ -93,6 +93,40 @@ __global__ void k_shift(uint32_t *__restrict__ img, int pitch, uint16_t *__restr
   }
 }
 
+// ---- lazy image compaction: refresh through the pending-removal lists, then add the removal ----
+__global__ void k_patch_lazy(const uint32_t *__restrict__ img, int pitch, int H, int W, const int32_t *__restrict__ seam,
+                             const int16_t *__restrict__ lists_in, int16_t *__restrict__ lists_out, int m,
+                             uint32_t *__restrict__ patch, int *err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= H) return;
+  bool bad = false;
+  patch[i] = patch_row_lazy(img, pitch, H, W, seam, lists_in, m, i, &bad);
+  if (bad) {
+    atomicOr(err, ERR_BAD_SEAM);
+    return;
+  }
+  list_insert(lists_in + (int64_t)i * RPEND, lists_out + (int64_t)i * RPEND, m, seam[i]);
+}
+
+// one warp per row: refreshed pair (lazy image), list update, energy compaction (refresh_row)
+__global__ void k_refresh(const uint32_t *__restrict__ img, int pitch, uint16_t *__restrict__ E, int pe, int H, int W,
+                          const int32_t *__restrict__ seam, const int16_t *__restrict__ lists_in,
+                          int16_t *__restrict__ lists_out, int m, int *err) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < H; i += warps)
+    if (!refresh_row(img, pitch, E, pe, H, W, seam, lists_in, lists_out, m, i, lane) && lane == 0)
+      atomicOr(err, ERR_BAD_SEAM);
+}
+
+__global__ void k_compact_lazy(uint32_t *__restrict__ img, int pitch, int H, int w, const int16_t *__restrict__ lists,
+                               int m) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < H; i += warps)
+    compact_row_lazy(img + (int64_t)i * pitch, lists + (int64_t)i * RPEND, m, w, lane);
+}
+
 // ---- launchers ----
 static int grid_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
@@ -151,6 +185,34 @@ cudaError_t launch_shift(uint32_t *img, int pitch, uint16_t *E, int pe, int H, i
   int blocks = (H + warps_per_block - 1) / warps_per_block;
   if (blocks > 152 * 8) blocks = 152 * 8;
   k_shift<<<blocks, warps_per_block * 32, 0, st>>>(img, pitch, E, pe, H, W, seam, patch);
+  return cudaGetLastError();
+}
+
+}  // namespace sc
+
+namespace sc {
+
+cudaError_t launch_patch_lazy(const uint32_t *img, int pitch, int H, int W, const int32_t *seam,
+                              const int16_t *lists_in, int16_t *lists_out, int m, uint32_t *patch, int *err,
+                              cudaStream_t st) {
+  k_patch_lazy<<<(H + 127) / 128, 128, 0, st>>>(img, pitch, H, W, seam, lists_in, lists_out, m, patch, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refresh(const uint32_t *img, int pitch, uint16_t *E, int pe, int H, int W, const int32_t *seam,
+                           const int16_t *lists_in, int16_t *lists_out, int m, int *err, cudaStream_t st) {
+  const int warps_per_block = 8;
+  int blocks = (H + warps_per_block - 1) / warps_per_block;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_refresh<<<blocks, warps_per_block * 32, 0, st>>>(img, pitch, E, pe, H, W, seam, lists_in, lists_out, m, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact_lazy(uint32_t *img, int pitch, int H, int w, const int16_t *lists, int m, cudaStream_t st) {
+  const int warps_per_block = 8;
+  int blocks = (H + warps_per_block - 1) / warps_per_block;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_compact_lazy<<<blocks, warps_per_block * 32, 0, st>>>(img, pitch, H, w, lists, m);
   return cudaGetLastError();
 }
 

@@ -99,3 +99,114 @@ __device__ __forceinline__ void unpack_pixel(uint32_t w, uint8_t *d, int C) {
 }
 
 }  // namespace sc
+
+namespace sc {
+
+// ---- lazy compaction of the image words ----
+// The stored words of a row are compacted only every RPEND seams. Between compactions each row
+// keeps the sorted stored columns o_0 < o_1 < ... < o_(m-1) of its m removed pixels. Current column
+// j (after the m removals) is stored column j + #{q : o_q - q <= j}: o_q - q is the number of kept
+// pixels left of o_q, so the q-th removal is passed exactly when j reaches it.
+constexpr int RPEND = 16;
+
+__device__ __forceinline__ int lazy_map(const int16_t *list, int m, int j) {
+  int c = 0;
+  for (int q = 0; q < m; ++q) c += ((int)list[q] - q <= j) ? 1 : 0;
+  return j + c;
+}
+
+// The two energies of row i that removing `seam` changes (as patch_row), with the image read
+// through the pending-removal lists `lists` (row r at lists + r*RPEND, m entries each) of the
+// width-W image the seam was found in.
+__device__ __forceinline__ uint32_t patch_row_lazy(const uint32_t *img, int pitch, int H, int W, const int32_t *seam,
+                                                   const int16_t *lists, int m, int i, bool *bad) {
+  const int Wn = W - 1;
+  const int s = seam[i];
+  if (s < 0 || s >= W) {
+    *bad = true;
+    return 0u;
+  }
+  auto pix = [&](int r, int j) -> uint32_t {
+    r = clampi(r, 0, H - 1);
+    j = clampi(j, 0, Wn - 1);
+    const int x = j + (j >= seam[r] ? 1 : 0);                    // column in the width-W image
+    return img[(int64_t)r * pitch + lazy_map(lists + (int64_t)r * RPEND, m, x)];
+  };
+  auto en = [&](int j) -> uint32_t { return sad4(pix(i, j + 1), pix(i, j - 1)) + sad4(pix(i + 1, j), pix(i - 1, j)); };
+  const uint32_t p0 = (s >= 1) ? en(s - 1) : 0u;
+  const uint32_t p1 = (s <= Wn - 1) ? en(s) : 0u;
+  return p0 | (p1 << 16);
+}
+
+// Add row i's removal (current column s, image of the old list) to its sorted list: out gets m+1.
+__device__ __forceinline__ void list_insert(const int16_t *in, int16_t *out, int m, int s) {
+  const int o = lazy_map(in, m, s);
+  int q = 0;
+  for (; q < m && in[q] < o; ++q) out[q] = in[q];
+  out[q] = (int16_t)o;
+  for (; q < m; ++q) out[q + 1] = in[q];
+}
+
+// Compact one row of stored words in place by one warp: current column j <- stored lazy_map(j), for
+// j < w. Sources never lie left of their destination and the row is processed left to right in
+// chunks read completely before they are written, so nothing is overwritten before it is read.
+__device__ __forceinline__ void compact_row_lazy(uint32_t *row, const int16_t *list, int m, int w, int lane) {
+  constexpr int R = 4;
+  int l[RPEND];   // o_q - q (the output column where the q-th removal is passed), padded high
+#pragma unroll
+  for (int q = 0; q < RPEND; ++q) l[q] = q < m ? (int)list[q] - q : 0x7FFFFFFF;
+  int first = w;   // columns left of the first removal keep their place
+  if (m > 0) first = l[0];
+  for (int base = first; base < w; base += 32 * R) {
+    uint32_t x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int j = base + r * 32 + lane;
+      if (j < w) {
+        int c = 0;
+#pragma unroll
+        for (int q = 0; q < RPEND; ++q) c += (l[q] <= j) ? 1 : 0;
+        x[r] = row[j + c];
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int j = base + r * 32 + lane;
+      if (j < w) row[j] = x[r];
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace sc
+
+namespace sc {
+
+// One warp, row i, after seam `seam` was found in the width-W energy map E (and image words read
+// through the pending-removal lists_in with m entries): the row's refreshed energy pair (lane 0,
+// through the lazy map), the row's list with this removal added (lists_out), then the energy row's
+// tail shifted left past the seam and the pair written at the new columns s-1 and s.
+// Returns false when the seam column is out of range (nothing is changed then).
+__device__ __forceinline__ bool refresh_row(const uint32_t *img, int pitch, uint16_t *E, int pe, int H, int W,
+                                            const int32_t *seam, const int16_t *lists_in, int16_t *lists_out, int m,
+                                            int i, int lane) {
+  const int s = seam[i];
+  if (s < 0 || s >= W) return false;
+  uint32_t p = 0;
+  if (lane == 0) {
+    bool bad = false;
+    p = patch_row_lazy(img, pitch, H, W, seam, lists_in, m, i, &bad);
+    list_insert(lists_in + (int64_t)i * RPEND, lists_out + (int64_t)i * RPEND, m, s);
+  }
+  p = __shfl_sync(0xffffffffu, p, 0);
+  uint16_t *er = E + (int64_t)i * pe;
+  shift_row(er, s, W, lane);
+  if (lane == 0) {
+    if (s >= 1) er[s - 1] = (uint16_t)(p & 0xFFFFu);
+    if (s <= W - 2) er[s] = (uint16_t)(p >> 16);
+  }
+  return true;
+}
+
+}  // namespace sc

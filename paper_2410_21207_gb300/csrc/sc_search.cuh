@@ -213,6 +213,10 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   unsigned long long lastmin = ~0ull;
   const int nt = p.gated ? 0 : (H + KT - 1) / KT;
   constexpr uint32_t ROW_BYTES = BW * 2;
+  // fields used inside the loops, held in registers (stores through the map pointers could
+  // otherwise force reloads of the argument struct)
+  const int pitch_e = p.pitch_e;
+  uint32_t *const Mrow = p.Mrow;
 
   if (producer) {
     // ---- energy staging: rows of columns [ext0 - KT, ext0 - KT + BW), one bulk copy per lane ----
@@ -228,7 +232,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
       if (lane == 0) mbar_arrive_expect_tx(&full[slot], (uint32_t)nrows * ROW_BYTES);
       __syncwarp();
       if (lane < nrows)
-        bulk_g2s(ring + (size_t)(slot * KT + lane) * BW, Estage + (size_t)(rbeg + lane) * p.pitch_e, ROW_BYTES,
+        bulk_g2s(ring + (size_t)(slot * KT + lane) * BW, Estage + (size_t)(rbeg + lane) * pitch_e, ROW_BYTES,
                  &full[slot]);
     }
   } else {
@@ -264,7 +268,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
         for (int r = 0; r < KT; ++r) dp_row(k, *reinterpret_cast<const uint2 *>(er + r * BW), oobm);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);   // this warp is done with the staged rows
-        row_events(r0 + KT - 1, k, H, W, c0, frame_base, cta_own, A, p.Mrow, p.pitch_e, ancT, OWC, lastmin);
+        row_events(r0 + KT - 1, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, lastmin);
       } else {
         // first tile (row 0 has no predecessor) or a ragged last tile
         for (int r = 0; r < KT; ++r) {
@@ -280,7 +284,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
           } else {
             dp_row(k, ev, oobm);
           }
-          row_events(i, k, H, W, c0, frame_base, cta_own, A, p.Mrow, p.pitch_e, ancT, OWC, lastmin);
+          row_events(i, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, lastmin);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);
@@ -369,6 +373,10 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   const int ok = misc0[0];
   const uint32_t best_m = (uint32_t)misc0[1];
   uint16_t *fd = fdir + (size_t)warp * KS * 32;
+  const uint16_t *const Ef = p.E;
+  int32_t *const seam_out = p.seam;
+  int32_t *const seam_log = p.seam_log;
+  int *const errw = p.err;
   for (int s = warp * cs + rank; ok && warp < G::FW && s < S; s += G::FW * cs) {
     const int jbs = jb0[s];
     const int jprev = (s > 0) ? jb0[s - 1] : jb0[S];
@@ -381,12 +389,12 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
 #pragma unroll
     for (int u = 0; u < 8; ++u) oob[u] = (xc + u < 0 || xc + u >= W) ? SENT : 0u;
     if (s == 0) {
-      const uint4 ev = *reinterpret_cast<const uint4 *>(p.E + xc);
+      const uint4 ev = *reinterpret_cast<const uint4 *>(Ef + xc);
       m[0] = ev.x & 0xFFFFu; m[1] = ev.x >> 16; m[2] = ev.y & 0xFFFFu; m[3] = ev.y >> 16;
       m[4] = ev.z & 0xFFFFu; m[5] = ev.z >> 16; m[6] = ev.w & 0xFFFFu; m[7] = ev.w >> 16;
     } else {
-      const uint4 a = *reinterpret_cast<const uint4 *>(p.Mrow + (size_t)s * p.pitch_e + xc);
-      const uint4 b = *reinterpret_cast<const uint4 *>(p.Mrow + (size_t)s * p.pitch_e + xc + 4);
+      const uint4 a = *reinterpret_cast<const uint4 *>(Mrow + (size_t)s * pitch_e + xc);
+      const uint4 b = *reinterpret_cast<const uint4 *>(Mrow + (size_t)s * pitch_e + xc + 4);
       m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w; m[4] = b.x; m[5] = b.y; m[6] = b.z; m[7] = b.w;
     }
 #pragma unroll
@@ -398,7 +406,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
 #pragma unroll
       for (int r = 0; r < CH; ++r) {
         const int i = rbeg + r;
-        if (i < re) eb[r] = *reinterpret_cast<const uint4 *>(p.E + (size_t)i * p.pitch_e + xc);
+        if (i < re) eb[r] = *reinterpret_cast<const uint4 *>(Ef + (size_t)i * pitch_e + xc);
       }
     };
     auto run_chunk = [&](const uint4 (&eb)[CH], int rbeg) {
@@ -445,25 +453,25 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
         uint32_t v = 0;
 #pragma unroll
         for (int u = 0; u < 8; ++u) if (u == (rel & 7)) v = m[u];
-        if (v != best_m) atomicOr(p.err, ERR_COST_MISMATCH);
+        if (v != best_m) atomicOr(errw, ERR_COST_MISMATCH);
       }
     }
     __syncwarp();
     if (lane == 0) {
       int j = jbs;
       for (int i = re - 1; i >= first; --i) {
-        p.seam[i] = j;
-        if (p.seam_log) p.seam_log[i] = j;
+        seam_out[i] = j;
+        if (seam_log) seam_log[i] = j;
         const int rel = j - x0;
-        if (rel < 0 || rel >= FILL_W) { atomicOr(p.err, ERR_FILL_MISMATCH); j = -1; break; }
+        if (rel < 0 || rel >= FILL_W) { atomicOr(errw, ERR_FILL_MISMATCH); j = -1; break; }
         const uint32_t dd = (fd[(i - rs) * 32 + (rel >> 3)] >> (2 * (rel & 7))) & 3u;
         j += (int)dd - 1;
       }
       if (s == 0 && j >= 0) {
-        p.seam[0] = j;
-        if (p.seam_log) p.seam_log[0] = j;
+        seam_out[0] = j;
+        if (seam_log) seam_log[0] = j;
       }
-      if (j != jprev) atomicOr(p.err, ERR_FILL_MISMATCH);
+      if (j != jprev) atomicOr(errw, ERR_FILL_MISMATCH);
     }
     __syncwarp();
   }

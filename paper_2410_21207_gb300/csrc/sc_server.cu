@@ -217,7 +217,7 @@ bool admit(sc_server *s) {
     d.H = r.H; d.W = r.W; d.C = r.C; d.target_w = r.tw; d.target_h = r.th;
     int sm = Smax;
     const size_t scratch = item_bytes(d, s->cfg, &sm);
-    if (batch_smem_bytes(s->cfg.nw, s->cfg.kt, sm) > 232448 - 64) break;
+    if (batch_smem_bytes(s->cfg.nw, s->cfg.kt, sm) > 232448 - 1024) break;
     const size_t nin = (size_t)r.H * r.W * r.C, nout = (size_t)r.th * r.tw * r.C;
     size_t oin, oout, osc;
     if (!s->arena.alloc(nin, &oin)) break;
