@@ -48,11 +48,12 @@ __device__ void batch_seam_pass(const BatchItem &it, uint32_t *words, int rows, 
   int16_t *lb[2] = {it.lists, it.lists + (size_t)rows * RPEND};
   // the staging ring is idle between searches: it holds the rows' refreshed pairs
   uint32_t *pairs = reinterpret_cast<uint32_t *>(smem + search_plan<NW, KT, false>(Smax).ring);
+  uint16_t *const Ecur = it.E + E_PADL;
   int cur = 0, m = 0;
   for (int t = 0; t < count; ++t) {
     const int w = cols - t;
     SearchArgs a;
-    a.E = it.E + E_PADL;
+    a.E = Ecur;
     a.pitch_e = it.pe;
     a.H = rows;
     a.W = w;
@@ -71,11 +72,11 @@ __device__ void batch_seam_pass(const BatchItem &it, uint32_t *words, int rows, 
     }
     if (bad) atomicOr(err, ERR_BAD_SEAM);
     __syncthreads();
-    // energy rows compacted past the seam, the pair at the new columns s-1 and s, one warp per row
+    // energy rows compacted past the seam in place, the pair at the new columns s-1 and s
     for (int i = warp; i < rows; i += nwarps) {
       const int s = it.seam[i];
       if (s < 0 || s >= w) continue;
-      uint16_t *er = it.E + E_PADL + (size_t)i * it.pe;
+      uint16_t *er = Ecur + (size_t)i * it.pe;
       shift_row(er, s, w, lane);
       if (lane == 0) {
         const uint32_t pr = pairs[i];

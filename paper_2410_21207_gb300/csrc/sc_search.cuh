@@ -212,7 +212,11 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
 
   unsigned long long lastmin = ~0ull;
   const int nt = p.gated ? 0 : (H + KT - 1) / KT;
-  constexpr uint32_t ROW_BYTES = BW * 2;
+  // single CTA: only the warps whose strips reach into [0, W) compute, and only their columns are
+  // staged (a cluster is sized to W, so all its warps work)
+  const int nwa = CL ? NW : min(NW, (W + Q - 1) / Q);
+  const bool active = warp < nwa;
+  const uint32_t ROW_BYTES = CL ? (uint32_t)BW * 2 : (uint32_t)(nwa * Q + 2 * KT) * 2;
   // fields used inside the loops, held in registers (stores through the map pointers could
   // otherwise force reloads of the argument struct)
   const int pitch_e = p.pitch_e;
@@ -242,6 +246,12 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
       const bool more = r0 + KT < H;
       const uint32_t g = st.tiles + t;
       const int slot = (int)(g % NSLOT);
+      if (!active) {
+        // outside the image: release the slot at once and keep the barrier count
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        if (more) named_bar_sync(NW * 32);
+        continue;
+      }
       if (!mbar_wait_bounded(&full[slot], (g / NSLOT) & 1u, WAIT_TIMEOUT_NS)) {
         if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
       }
