@@ -43,8 +43,9 @@ def _args():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (Poisson trace) measurement")
     ap.add_argument("--no-4k", action="store_true", help="skip the 3840x2160 measurement")
     ap.add_argument("--serving-requests", type=int, default=300)
-    ap.add_argument("--profile-search", metavar="HxW", default=None,
-                    help="only call sc_find_seam a few times on a seeded HxW energy map (for ncu captures)")
+    ap.add_argument("--profile-search", metavar="HxW[xB]", default=None,
+                    help="only call sc_find_seam a few times on a seeded HxW energy map, or sc_find_seam_multi "
+                         "on B maps (for ncu captures)")
     return ap.parse_args()
 
 
@@ -298,16 +299,66 @@ def fourk_measurement(sc, torch, dev, flush, steps):
             "ms_per_carve": 1e3 * t}
 
 
+def uhd_search_measurement(sc, torch, dev, steps, peak):
+    """The energy+DP pass at 3840x2160 with B independent maps in flight (one cluster each, B = how
+    many fit on the GPU at once): the bandwidth view of the search, next to the single-map latency
+    chain. Algorithmic bytes = H*W*2.25 per map (energy read + one direction record)."""
+    import numpy as np
+    from paper_2410_21207_gb300 import synth
+    import oracle
+    H, W = 2160, 3840
+    B = max(1, sc.find_seam_multi_capacity(H, W))
+    e = oracle.energy(synth.config3().make()).astype(np.uint16)
+    maps = [torch.from_numpy(np.ascontiguousarray(np.roll(e, 37 * k, axis=1))).to(dev) for k in range(B)]
+    for _ in range(3):
+        sc.find_seam_multi(maps)
+    torch.cuda.synchronize(dev)
+    ms = []
+    for _ in range(max(5, steps)):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sc.find_seam_multi(maps)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    sc.timing_reset()
+    sc.timing_enable(True)
+    for _ in range(max(5, steps)):
+        sc.find_seam_multi(maps)
+    torch.cuda.synchronize(dev)
+    sc.timing_enable(False)
+    k_ms, k_n = sc.timing_read("dp_multi")
+    sc.check()
+    t = statistics.median(ms) / 1000.0
+    tk = k_ms / 1000.0 / max(k_n, 1)
+    alg = 2.25 * H * W * B
+    return {"workload": f"energy+DP pass (seam search) on {B} concurrent 3840x2160 maps", "maps": B,
+            "us_per_call": 1e6 * t, "seams_per_s": B / t, "mpix_seam_per_s": B * H * W / 1e6 / t,
+            "kernel": "k_dp_multi", "kernel_us_per_launch": 1e6 * tk,
+            "algorithmic_bytes_per_launch": alg, "achieved_gbs": alg / tk / 1e9,
+            "peak_gbs": peak, "frac": alg / tk / 1e9 / peak if peak else None,
+            "note": "working set B x 16.6 MB exceeds L2, so no flush; the call also copies each map into "
+                    "its padded workspace (one extra kernel per map), the kernel figure excludes that"}
+
+
 def profile_search(spec: str):
-    """sc_find_seam four times on a seeded H x W uint16 energy map (the kernel to capture is k_dp)."""
+    """sc_find_seam four times on a seeded H x W uint16 energy map (the kernel to capture is k_dp);
+    with HxWxB, sc_find_seam_multi on B shifted copies (the kernel is k_dp_multi)."""
     import numpy as np
     import torch
     from paper_2410_21207_gb300 import binding as sc
-    H, W = (int(x) for x in spec.lower().split("x"))
+    dims = [int(x) for x in spec.lower().split("x")]
+    H, W = dims[0], dims[1]
+    B = dims[2] if len(dims) > 2 else 0
     e = np.random.default_rng(0).integers(0, 1531, size=(H, W)).astype(np.uint16)
     t = torch.from_numpy(e).to("cuda:0")
+    maps = [torch.from_numpy(np.ascontiguousarray(np.roll(e, 37 * k, axis=1))).to("cuda:0") for k in range(B)]
     for _ in range(4):
-        sc.find_seam(t)
+        if B:
+            sc.find_seam_multi(maps)
+        else:
+            sc.find_seam(t)
     torch.cuda.synchronize()
     sc.check()
     print(json.dumps({"profile_search": spec, "ok": True}))
@@ -460,6 +511,8 @@ def run_native(a):
         line["batched"] = batched_measurement(sc, torch, dev, flush, a.steps)
     if rank == 0 and not a.no_4k:
         line["uhd_3840x2160"] = fourk_measurement(sc, torch, dev, flush, a.steps)
+    if rank == 0 and not a.no_4k:
+        line["uhd_search_concurrent"] = uhd_search_measurement(sc, torch, dev, a.steps, peak)
     if rank == 0 and serving_imgs is not None:
         line["serving"] = serving_measurement(sc, torch, dev, serving_imgs, a.serving_requests)
     if rank == 0 and not a.no_cpu_baseline and ws == 1:

@@ -96,6 +96,24 @@ int sc_energy(const uint8_t *img, int H, int W, int C, uint16_t *energy_out, voi
  *         or energies that could overflow (checked on the device: SC_EINTERNAL via sc_check). */
 int sc_find_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_t *cost_out, void *stream);
 
+/* ---- the same search for n independent maps of one size, in one launch ----
+ * The Algorithm 3 seam (DP fill, last-row argmin, backtrack) of each map, independently.
+ * energies: HOST array of n DEVICE pointers, each H x W uint16 row-major (as sc_find_seam).
+ * seams_out: device int32[n*H] (map k's seam at seams_out + k*H); costs_out: device int64[n] or
+ * NULL. One thread-block cluster per map; the clusters share the GPU, so with several maps in
+ * flight the pass is bound by memory bandwidth rather than by one map's chain of dependent rows.
+ * Results equal n calls of sc_find_seam. Errors: as sc_find_seam; n < 1 -> SC_EINVAL. */
+int sc_find_seam_multi(const uint16_t *const *energies, int n, int H, int W, int32_t *seams_out, int64_t *costs_out,
+                       void *stream);
+
+/* How many H x W searches of sc_find_seam_multi are resident on the current device at once
+ * (thread-block clusters that fit together); a batch of that many maps fills the GPU. */
+int sc_find_seam_multi_capacity(int H, int W, int *n_out);
+
+/* Tile shape of sc_find_seam_multi: compute warps per CTA (4 or 8) and DP tile rows (8 or 16);
+ * (0, 0) restores the automatic choice. Process-wide. Any other pair -> SC_EINVAL. */
+int sc_find_seam_multi_shape(int warps, int tile_rows);
+
 /* ---- sc_find_seam without allocation (the paper has no counterpart: this is a deployment aid) ----
  * For programs that must not let a library allocate device memory: cudaMalloc/cudaFree can
  * synchronise the device and take unpredictable time inside a latency-critical loop, and hosts

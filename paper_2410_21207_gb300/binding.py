@@ -62,6 +62,9 @@ def load(path: Optional[str] = None):
                 "sc_energy": ([P, I, I, I, P, P], I),
                 "sc_find_seam": ([P, I, I, P, P, P], I),
                 "sc_find_seam_static": ([P, I, I, P, P, P], I),
+                "sc_find_seam_multi": ([P, I, I, I, P, P, P], I),
+                "sc_find_seam_multi_capacity": ([I, I, P], I),
+                "sc_find_seam_multi_shape": ([I, I], I),
                 "sc_carve": ([P, I, I, I, I, I, P, P, P, P], I),
                 "sc_carve_plain": ([P, I, I, I, I, I, P, P, P, P], I),
                 "sc_carve_host": ([P, I, I, I, I, I, P, P], I),
@@ -145,6 +148,39 @@ def find_seam(e):
     cost = torch.empty(1, dtype=torch.int64, device=e.device)
     _raise(load().sc_find_seam(_ptr(e), H, W, _ptr(seam), _ptr(cost), _stream(torch, e.device)))
     return seam, cost
+
+
+def find_seam_multi(energies):
+    """The Algorithm 3 search of n same-size H x W uint16 CUDA maps in one launch (one cluster per
+    map) -> (int32[n, H] seams, int64[n] costs); equal to n calls of find_seam."""
+    torch = _torch()
+    es = list(energies)
+    if not es:
+        raise ValueError("need at least one energy map")
+    H, W = es[0].shape
+    for e in es:
+        if (e.device.type != "cuda" or e.dtype != torch.uint16 or e.dim() != 2 or not e.is_contiguous()
+                or tuple(e.shape) != (H, W) or e.device != es[0].device):
+            raise ValueError("energies must be contiguous H x W uint16 CUDA tensors of one shape and device")
+    n = len(es)
+    seams = torch.empty((n, H), dtype=torch.int32, device=es[0].device)
+    costs = torch.empty(n, dtype=torch.int64, device=es[0].device)
+    ptrs = (ctypes.c_void_p * n)(*[e.data_ptr() for e in es])
+    _raise(load().sc_find_seam_multi(ptrs, n, H, W, _ptr(seams), _ptr(costs), _stream(torch, es[0].device)))
+    return seams, costs
+
+
+def find_seam_multi_capacity(H: int, W: int) -> int:
+    """How many H x W maps find_seam_multi keeps resident at once on the current device."""
+    _torch()
+    n = ctypes.c_int(0)
+    _raise(load().sc_find_seam_multi_capacity(H, W, ctypes.byref(n)))
+    return n.value
+
+
+def find_seam_multi_shape(warps: int = 0, tile_rows: int = 0) -> None:
+    """Fix find_seam_multi's tile shape (compute warps per CTA, DP tile rows); (0, 0) = automatic."""
+    _raise(load().sc_find_seam_multi_shape(warps, tile_rows))
 
 
 def find_seam_static(e):

@@ -103,10 +103,14 @@ struct Workspace {
   DevBuf<int16_t> lists;          // two generations of pending-removal lists
   DevBuf<uint8_t> hin, hout;     // staging for the host-pointer entry point
   DevBuf<int> flags;             // [0] error word, [1] energy-range gate
+  DevBuf<uint16_t> Emulti;       // padded maps of sc_find_seam_multi
+  DevBuf<uint32_t> Mmulti;
+  DevBuf<DpArgs> dargs;
   bool flags_zeroed = false;
   void release_all() {
     img.release(); img2.release(); Mrow.release(); patch.release();
     E.release(); seam.release(); lists.release(); hin.release(); hout.release(); flags.release();
+    Emulti.release(); Mmulti.release(); dargs.release();
     flags_zeroed = false;
   }
 };
@@ -394,6 +398,60 @@ int sc_find_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_
   SC_CUDA(cudaMemsetAsync(ws.flags.p + 1, 0, sizeof(int), st));
   SC_CUDA(launch_copy_energy(energy, H, W, ws.E.p + E_PADL, pe, ws.flags.p, ws.flags.p + 1, st));
   return launch_search(ws, ws.E.p, pe, H, W, seam_out, nullptr, cost_out, ws.flags.p + 1, st);
+}
+
+int sc_find_seam_multi(const uint16_t *const *energies, int n, int H, int W, int32_t *seams_out, int64_t *costs_out,
+                       void *stream) {
+  if (!energies || !seams_out || n < 1) return fail(SC_EINVAL, "null pointer or empty batch");
+  if (H < 1 || W < 1 || H > SC_MAX_ROWS || W > SC_MAX_COLS) return fail(SC_EINVAL, "bad shape %d x %d", H, W);
+  for (int k = 0; k < n; ++k)
+    if (!energies[k]) return fail(SC_EINVAL, "null energy map %d", k);
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace *wsp;
+  int rc = get_ws(stream, &wsp);
+  if (rc) return rc;
+  Workspace &ws = *wsp;
+  std::lock_guard<std::mutex> lk(ws.mu);
+  if ((rc = ensure_flags(ws, st))) return rc;
+  const int pe = pitch_e_for(W);
+  const int S = (H + KS - 1) / KS;
+  const size_t e_per = (size_t)H * pe, m_per = (size_t)(S + 1) * pe;
+  SC_CUDA(ws.Emulti.ensure(e_per * n));
+  SC_CUDA(ws.Mmulti.ensure(m_per * n));
+  SC_CUDA(ws.dargs.ensure((size_t)n));
+  SC_CUDA(cudaMemsetAsync(ws.flags.p + 1, 0, sizeof(int), st));
+  std::vector<DpArgs> h(n);
+  for (int k = 0; k < n; ++k) {
+    uint16_t *Ek = ws.Emulti.p + e_per * k;
+    SC_CUDA(launch_copy_energy(energies[k], H, W, Ek + E_PADL, pe, ws.flags.p, ws.flags.p + 1, st));
+    DpArgs &a = h[k];
+    a.E = Ek + E_PADL;
+    a.pitch_e = pe;
+    a.H = H;
+    a.W = W;
+    a.Mrow = ws.Mmulti.p + m_per * k + E_PADL;
+    a.seam = seams_out + (size_t)k * H;
+    a.seam_log = nullptr;
+    a.cost = costs_out ? costs_out + k : nullptr;
+    a.err = ws.flags.p;
+    a.gate = ws.flags.p + 1;
+  }
+  SC_CUDA(cudaMemcpyAsync(ws.dargs.p, h.data(), n * sizeof(DpArgs), cudaMemcpyHostToDevice, st));
+  SC_CUDA(timed("dp_multi", st, [&] { return launch_dp_multi(ws.dargs.p, n, H, W, st); }));
+  return SC_OK;
+}
+
+int sc_find_seam_multi_capacity(int H, int W, int *n_out) {
+  if (!n_out) return fail(SC_EINVAL, "null pointer");
+  if (H < 1 || W < 1 || H > SC_MAX_ROWS || W > SC_MAX_COLS) return fail(SC_EINVAL, "bad shape %d x %d", H, W);
+  SC_CUDA(dp_multi_capacity(H, W, n_out));
+  return SC_OK;
+}
+
+int sc_find_seam_multi_shape(int warps, int tile_rows) {
+  if (dp_multi_set_shape(warps, tile_rows) != 0)
+    return fail(SC_EINVAL, "no multi-search shape with %d warps and %d-row tiles", warps, tile_rows);
+  return SC_OK;
 }
 
 int sc_carve_plain(const uint8_t *img, int H, int W, int C, int target_w, int target_h, uint8_t *out,

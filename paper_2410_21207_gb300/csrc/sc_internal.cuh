@@ -72,6 +72,13 @@ cudaError_t launch_patch(const uint32_t *img, int pitch_img, int H, int W, const
 cudaError_t launch_shift(uint32_t *img, int pitch_img, uint16_t *E, int pitch_e, int H, int W, const int32_t *seam,
                          const uint32_t *patch, cudaStream_t st);
 cudaError_t launch_dp(const DpArgs &a, cudaStream_t st);
+// n searches of H x W maps in one launch (one cluster each); dargs_dev is a device array
+cudaError_t launch_dp_multi(const DpArgs *dargs_dev, int n, int H, int W, cudaStream_t st);
+// how many H x W searches of launch_dp_multi are resident on the GPU at once
+cudaError_t dp_multi_capacity(int H, int W, int *n_out);
+// tile shape of launch_dp_multi: (compute warps per CTA, tile rows), (0, 0) = automatic;
+// returns -1 for a shape that is not built
+int dp_multi_set_shape(int nw, int kt);
 // lazy image compaction (sc_rowops.cuh): refresh + list update per seam, bulk compaction
 cudaError_t launch_patch_lazy(const uint32_t *img, int pitch, int H, int W, const int32_t *seam,
                               const int16_t *lists_in, int16_t *lists_out, int m, uint32_t *patch, int *err,

@@ -45,13 +45,13 @@ constexpr int FILL_W = 256;              // backtrack-fill window (8 columns per
 constexpr int FILL_WARPS_MAX = 8;        // warps that run backtrack fills
 constexpr int NSLOT = 3;                 // energy staging ring: tiles in flight
 
-template <int NW, int KT, bool CL>
+template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX>
 struct Geo {
   static constexpr int Q = 32 * V - 2 * KT;              // warp strip
   static constexpr int K2E = CL ? K2 : 0;                // CTA-level halo (clusters only)
   static constexpr int BW = NW * Q + 2 * KT;             // boundary / staged row width
   static constexpr int OWC = NW * Q - 2 * K2E;           // CTA-own columns
-  static constexpr int FW = (NW + 1) < FILL_WARPS_MAX ? (NW + 1) : FILL_WARPS_MAX;
+  static constexpr int FW = (NW + 1) < FWM ? (NW + 1) : FWM;   // backtrack-fill warps
   static constexpr int THREADS = (NW + 1) * 32;          // compute warps + the producer warp
   static_assert(Q > 0 && KS % KT == 0 && K2 % KT == 0, "tile geometry");
   static_assert(Q + 2 * KS <= 256, "the ancestor frame must fit 8 bits");
@@ -62,9 +62,9 @@ struct SearchPlan {
   size_t bnd, hbuf, anc, wmin, cmin, jb, misc, fdir, ring, bars, total;
 };
 
-template <int NW, int KT, bool CL>
+template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX>
 __host__ __device__ inline SearchPlan search_plan(int S) {
-  using G = Geo<NW, KT, CL>;
+  using G = Geo<NW, KT, CL, FWM>;
   SearchPlan p;
   size_t o = 0;
   p.bnd = o;  o += (size_t)2 * G::BW * 4;  o = (o + 15) & ~(size_t)15;
@@ -147,11 +147,26 @@ __device__ __forceinline__ void dp_row(uint32_t (&k)[V], uint2 ev, const uint32_
   k[0] = n0; k[1] = n1; k[2] = n2; k[3] = n3;
 }
 
+// KT rows of a full tile from the staged energies er (row stride BW); MASK applies oobm.
+template <int KT, int BW, bool MASK>
+__device__ __forceinline__ void dp_rows(uint32_t (&k)[V], const uint16_t *er, const uint32_t (&oobm)[V]) {
+  constexpr uint32_t Z[V] = {0u, 0u, 0u, 0u};
+  uint2 a = *reinterpret_cast<const uint2 *>(er);
+  uint2 b = *reinterpret_cast<const uint2 *>(er + BW);
+#pragma unroll
+  for (int r = 0; r < KT; ++r) {
+    const uint2 ev = a;
+    a = b;
+    if (r + 2 < KT) b = *reinterpret_cast<const uint2 *>(er + (r + 2) * BW);
+    dp_row(k, ev, MASK ? oobm : Z);
+  }
+}
+
 // Initialise the staging and halo mbarriers (thread 0; the caller then synchronises the CTA, and
 // the cluster when CL).
-template <int NW, int KT, bool CL>
+template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX>
 __device__ inline void search_init(unsigned char *smem, int S) {
-  const SearchPlan plan = search_plan<NW, KT, CL>(S);
+  const SearchPlan plan = search_plan<NW, KT, CL, FWM>(S);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + plan.bars);
   uint64_t *empty = full + NSLOT;
   uint64_t *hbar = empty + NSLOT;
@@ -173,9 +188,9 @@ __device__ __forceinline__ void group_sync() {
 
 // The search. Every thread of the CTA (of every CTA of the cluster when CL) calls it with the same
 // arguments; `Smax` is the super-tile count the shared-memory plan was sized for.
-template <int NW, int KT, bool CL>
+template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX>
 __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, SearchState &st) {
-  using G = Geo<NW, KT, CL>;
+  using G = Geo<NW, KT, CL, FWM>;
   constexpr int Q = G::Q, BW = G::BW, OWC = G::OWC, K2E = G::K2E;
   const int rank = CL ? (int)cg::this_cluster().block_rank() : 0;
   const int cs = CL ? (int)cg::this_cluster().num_blocks() : 1;
@@ -183,7 +198,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   const bool producer = (warp == NW);
   const int H = p.H, W = p.W;
   const int S = (H + KS - 1) / KS;
-  const SearchPlan plan = search_plan<NW, KT, CL>(Smax);
+  const SearchPlan plan = search_plan<NW, KT, CL, FWM>(Smax);
   uint32_t *bnd = reinterpret_cast<uint32_t *>(smem + plan.bnd);
   uint32_t *hbuf = reinterpret_cast<uint32_t *>(smem + plan.hbuf);
   uint8_t *ancT = reinterpret_cast<uint8_t *>(smem + plan.anc);
@@ -208,6 +223,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   uint32_t oobm[V];
 #pragma unroll
   for (int u = 0; u < V; ++u) oobm[u] = (c0 + u < 0 || c0 + u >= W) ? SENT : 0u;
+  const bool edge = __any_sync(0xffffffffu, (oobm[0] | oobm[V - 1]) != 0u);
   const int bidx0 = c0 - (ext0 - KT);           // index of c0 in bnd and in a staged energy row
 
   unsigned long long lastmin = ~0ull;
@@ -273,9 +289,11 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
         k[0] |= oobm[0]; k[1] |= oobm[1]; k[2] |= oobm[2]; k[3] |= oobm[3];
       }
       if (t > 0 && !(r0 + KT > H)) {
-        // full tile: KT branch-free rows, bookkeeping only on its last row
-#pragma unroll
-        for (int r = 0; r < KT; ++r) dp_row(k, *reinterpret_cast<const uint2 *>(er + r * BW), oobm);
+        // full tile: KT branch-free rows, bookkeeping only on its last row. The energies of the
+        // next rows are loaded ahead of the row that needs them, off the dependent chain; only
+        // warps that hold columns outside the image apply the exclusion mask.
+        if (edge) dp_rows<KT, BW, true>(k, er, oobm);
+        else dp_rows<KT, BW, false>(k, er, oobm);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);   // this warp is done with the staged rows
         row_events(r0 + KT - 1, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, lastmin);

@@ -51,3 +51,9 @@ def test_argument_errors_are_synchronous():
     assert lib.sc_find_seam(fake, 10, binding.MAX_COLS + 1, fake, P(0), P(0)) == binding.SC_EINVAL
     assert lib.sc_energy(fake, 10, 10, 5, fake, P(0)) == binding.SC_EINVAL
     assert lib.sc_carve_batch(P(0), 0, P(0)) == binding.SC_EINVAL
+    assert lib.sc_find_seam_multi_shape(5, 8) == binding.SC_EINVAL
+    assert lib.sc_find_seam_multi_shape(0, 0) == binding.SC_OK
+    maps = (P * 2)(fake, P(0))
+    assert lib.sc_find_seam_multi(maps, 0, 10, 10, fake, P(0), P(0)) == binding.SC_EINVAL
+    assert lib.sc_find_seam_multi(maps, 2, 10, 10, fake, P(0), P(0)) == binding.SC_EINVAL   # null map
+    assert lib.sc_find_seam_multi(maps, 1, 10, binding.MAX_COLS + 1, fake, P(0), P(0)) == binding.SC_EINVAL

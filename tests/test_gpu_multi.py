@@ -1,0 +1,95 @@
+"""Parity of sc_find_seam_multi (n maps of one size searched in one launch, one cluster per map)
+with the oracle's Algorithm 3 seam of each map, including full 3840 x 2160 maps."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_21207_gb300 import binding as sc
+from paper_2410_21207_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.fail("the -m gpu tests need a CUDA GPU")
+    return torch.device("cuda:0")
+
+
+def _maps(rng, n, H, W):
+    kinds = [
+        lambda: rng.integers(0, 1531, size=(H, W)),
+        lambda: rng.integers(0, 3, size=(H, W)),                 # many exact ties
+        lambda: np.full((H, W), 5),                              # constant: leftmost straight seam
+        lambda: np.tile(rng.integers(0, 40, size=(1, W)), (H, 1)),
+    ]
+    return [kinds[k % len(kinds)]().astype(np.uint16) for k in range(n)]
+
+
+def _check(dev, maps):
+    got_s, got_c = sc.find_seam_multi([torch.from_numpy(m).to(dev) for m in maps])
+    sc.check()
+    got_s, got_c = got_s.cpu().numpy(), got_c.cpu().numpy()
+    for k, m in enumerate(maps):
+        s_ref, c_ref = oracle.dp_seam(m)
+        assert int(got_c[k]) == c_ref, k
+        np.testing.assert_array_equal(got_s[k], s_ref, err_msg=f"map {k} of {len(maps)}, {m.shape}")
+
+
+SHAPES = [(8, 8), (8, 16), (4, 8), (4, 16)]   # (compute warps per CTA, DP tile rows)
+OWN_COLS = {(8, 8): 768, (8, 16): 640, (4, 8): 320, (4, 16): 256}   # columns each CTA owns
+
+
+@pytest.fixture
+def shape(request):
+    sc.find_seam_multi_shape(*request.param)
+    yield request.param
+    sc.find_seam_multi_shape(0, 0)
+
+
+@pytest.mark.parametrize("shape", SHAPES, indirect=True)
+@pytest.mark.parametrize("H,W,n", [(1, 1, 1), (1, 300, 3), (17, 96, 4), (65, 257, 5), (130, 700, 7),
+                                   (300, 2049, 3), (200, 3840, 6), (64, 8192, 2), (2000, 40, 3)])
+def test_multi_parity(dev, shape, H, W, n):
+    if OWN_COLS[shape] * 16 < W:
+        with pytest.raises(sc.ScError):
+            sc.find_seam_multi([torch.zeros((H, W), dtype=torch.uint16, device=dev)])
+        return
+    rng = np.random.default_rng(H * 131 + W * 7 + n)
+    _check(dev, _maps(rng, n, H, W))
+
+
+def test_multi_shape_rejected():
+    with pytest.raises(sc.ScError):
+        sc.find_seam_multi_shape(5, 8)
+
+
+def test_multi_equals_single(dev):
+    rng = np.random.default_rng(5)
+    maps = [torch.from_numpy(m).to(dev) for m in _maps(rng, 9, 333, 1500)]
+    s_multi, c_multi = sc.find_seam_multi(maps)
+    for k, m in enumerate(maps):
+        s1, c1 = sc.find_seam(m)
+        assert torch.equal(s_multi[k], s1) and int(c_multi[k]) == int(c1[0])
+    sc.check()
+
+
+@pytest.mark.parametrize("shape", SHAPES + [(0, 0)], indirect=True)
+def test_multi_uhd(dev, shape):
+    """Full 3840 x 2160 maps: the energy of the 4K synthetic image, its mirror, and two random maps."""
+    job = synth.config3()
+    e = oracle.energy(job.make())
+    rng = np.random.default_rng(2160)
+    maps = [e.astype(np.uint16), np.ascontiguousarray(e[:, ::-1]).astype(np.uint16)] + _maps(rng, 2, 2160, 3840)
+    _check(dev, maps)
+
+
+def test_multi_energy_range_rejected(dev):
+    e = np.full((2000, 16), 60000, dtype=np.uint16)   # 2000 * 60000 >= 2^24
+    sc.find_seam_multi([torch.from_numpy(e).to(dev)] * 2)
+    with pytest.raises(sc.ScError) as ei:
+        sc.check()
+    assert ei.value.code == sc.SC_EINVAL
+    sc.check()
