@@ -97,7 +97,7 @@ struct DevBuf {
 
 struct Workspace {
   std::mutex mu;
-  DevBuf<uint32_t> img, img2, Mrow, patch;
+  DevBuf<uint32_t> img, img2, Mrow;
   DevBuf<uint16_t> E;
   DevBuf<int32_t> seam;
   DevBuf<int16_t> lists;          // two generations of pending-removal lists
@@ -108,7 +108,7 @@ struct Workspace {
   DevBuf<DpArgs> dargs;
   bool flags_zeroed = false;
   void release_all() {
-    img.release(); img2.release(); Mrow.release(); patch.release();
+    img.release(); img2.release(); Mrow.release();
     E.release(); seam.release(); lists.release(); hin.release(); hout.release(); flags.release();
     Emulti.release(); Mmulti.release(); dargs.release();
     flags_zeroed = false;
@@ -167,7 +167,6 @@ static int ensure_carve_buffers(Workspace &ws, int H, int W) {
   const int S = (R + KS - 1) / KS;
   SC_CUDA(ws.Mrow.ensure((size_t)(S + 1) * pe));
   SC_CUDA(ws.seam.ensure((size_t)R));
-  SC_CUDA(ws.patch.ensure((size_t)R));
   SC_CUDA(ws.lists.ensure((size_t)2 * R * RPEND));
   return SC_OK;
 }

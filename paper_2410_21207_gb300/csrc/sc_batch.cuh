@@ -77,7 +77,7 @@ __device__ void batch_seam_pass(const BatchItem &it, uint32_t *words, int rows, 
       const int s = it.seam[i];
       if (s < 0 || s >= w) continue;
       uint16_t *er = Ecur + (size_t)i * it.pe;
-      shift_row(er, s, w, lane);
+      shift_row_u16(er, s, w, lane);
       if (lane == 0) {
         const uint32_t pr = pairs[i];
         if (s >= 1) er[s - 1] = (uint16_t)(pr & 0xFFFFu);

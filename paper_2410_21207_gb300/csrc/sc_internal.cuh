@@ -67,10 +67,6 @@ cudaError_t launch_energy(const uint32_t *img, int pitch_img, int H, int W, uint
 cudaError_t launch_copy_energy(const uint16_t *src, int H, int W, uint16_t *E, int pitch_e, int *err, int *gate,
                                cudaStream_t st);
 cudaError_t launch_unpad_energy(const uint16_t *E, int pitch_e, int H, int W, uint16_t *dst, cudaStream_t st);
-cudaError_t launch_patch(const uint32_t *img, int pitch_img, int H, int W, const int32_t *seam, uint32_t *patch,
-                         int *err, cudaStream_t st);
-cudaError_t launch_shift(uint32_t *img, int pitch_img, uint16_t *E, int pitch_e, int H, int W, const int32_t *seam,
-                         const uint32_t *patch, cudaStream_t st);
 cudaError_t launch_dp(const DpArgs &a, cudaStream_t st);
 // n searches of H x W maps in one launch (one cluster each); dargs_dev is a device array
 cudaError_t launch_dp_multi(const DpArgs *dargs_dev, int n, int H, int W, cudaStream_t st);
@@ -80,9 +76,6 @@ cudaError_t dp_multi_capacity(int H, int W, int *n_out);
 // returns -1 for a shape that is not built
 int dp_multi_set_shape(int nw, int kt);
 // lazy image compaction (sc_rowops.cuh): refresh + list update per seam, bulk compaction
-cudaError_t launch_patch_lazy(const uint32_t *img, int pitch, int H, int W, const int32_t *seam,
-                              const int16_t *lists_in, int16_t *lists_out, int m, uint32_t *patch, int *err,
-                              cudaStream_t st);
 cudaError_t launch_compact_lazy(uint32_t *img, int pitch, int H, int w, const int16_t *lists, int m, cudaStream_t st);
 // per seam: refreshed pair through the lazy map, list update and energy compaction (one warp per row)
 cudaError_t launch_refresh(const uint32_t *img, int pitch, uint16_t *E, int pe, int H, int W, const int32_t *seam,

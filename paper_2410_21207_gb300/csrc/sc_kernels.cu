@@ -71,43 +71,7 @@ __global__ void k_unpad_energy(const uint16_t *__restrict__ E, int pe, int H, in
   dst[(int64_t)i * W + j] = E[(int64_t)i * pe + j];
 }
 
-// ---- local refresh: the two energies per row that the removal changes (patch_row) ----
-__global__ void k_patch(const uint32_t *__restrict__ img, int pitch, int H, int W, const int32_t *__restrict__ seam,
-                        uint32_t *__restrict__ patch, int *err) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= H) return;
-  bool bad = false;
-  patch[i] = patch_row(img, pitch, H, W, seam, i, &bad);
-  if (bad) atomicOr(err, ERR_BAD_SEAM);
-}
-
-// ---- compaction: one warp per row, in place (compact_row) ----
-__global__ void k_shift(uint32_t *__restrict__ img, int pitch, uint16_t *__restrict__ E, int pe, int H, int W,
-                        const int32_t *__restrict__ seam, const uint32_t *__restrict__ patch) {
-  const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < H; i += warps) {
-    const int s = seam[i];
-    if (s < 0 || s >= W) continue;   // recorded by k_patch
-    compact_row(img, pitch, E, pe, W, s, patch[i], i, lane);
-  }
-}
-
 // ---- lazy image compaction: refresh through the pending-removal lists, then add the removal ----
-__global__ void k_patch_lazy(const uint32_t *__restrict__ img, int pitch, int H, int W, const int32_t *__restrict__ seam,
-                             const int16_t *__restrict__ lists_in, int16_t *__restrict__ lists_out, int m,
-                             uint32_t *__restrict__ patch, int *err) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= H) return;
-  bool bad = false;
-  patch[i] = patch_row_lazy(img, pitch, H, W, seam, lists_in, m, i, &bad);
-  if (bad) {
-    atomicOr(err, ERR_BAD_SEAM);
-    return;
-  }
-  list_insert(lists_in + (int64_t)i * RPEND, lists_out + (int64_t)i * RPEND, m, seam[i]);
-}
-
 // one warp per row: refreshed pair (lazy image), list update, energy compaction (refresh_row)
 __global__ void k_refresh(const uint32_t *__restrict__ img, int pitch, uint16_t *__restrict__ E, int pe, int H, int W,
                           const int32_t *__restrict__ seam, const int16_t *__restrict__ lists_in,
@@ -173,31 +137,9 @@ cudaError_t launch_unpad_energy(const uint16_t *E, int pe, int H, int W, uint16_
   return cudaGetLastError();
 }
 
-cudaError_t launch_patch(const uint32_t *img, int pitch, int H, int W, const int32_t *seam, uint32_t *patch, int *err,
-                         cudaStream_t st) {
-  k_patch<<<(H + 127) / 128, 128, 0, st>>>(img, pitch, H, W, seam, patch, err);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_shift(uint32_t *img, int pitch, uint16_t *E, int pe, int H, int W, const int32_t *seam,
-                         const uint32_t *patch, cudaStream_t st) {
-  const int warps_per_block = 8;
-  int blocks = (H + warps_per_block - 1) / warps_per_block;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  k_shift<<<blocks, warps_per_block * 32, 0, st>>>(img, pitch, E, pe, H, W, seam, patch);
-  return cudaGetLastError();
-}
-
 }  // namespace sc
 
 namespace sc {
-
-cudaError_t launch_patch_lazy(const uint32_t *img, int pitch, int H, int W, const int32_t *seam,
-                              const int16_t *lists_in, int16_t *lists_out, int m, uint32_t *patch, int *err,
-                              cudaStream_t st) {
-  k_patch_lazy<<<(H + 127) / 128, 128, 0, st>>>(img, pitch, H, W, seam, lists_in, lists_out, m, patch, err);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_refresh(const uint32_t *img, int pitch, uint16_t *E, int pe, int H, int W, const int32_t *seam,
                            const int16_t *lists_in, int16_t *lists_out, int m, int *err, cudaStream_t st) {

@@ -1,6 +1,6 @@
 // Per-pixel and per-row operations shared by the whole-image kernels (sc_kernels.cu) and the
 // batched persistent kernel (sc_batch.cuh): the e1 energy of a pixel ("Energy Mapping", item e1),
-// the two refreshed energies of a row after a removal, and the in-place row compaction ("Removal of
+// the two refreshed energies of a row after a removal, and the row compactions ("Removal of
 // Seams"). Pixels are uint32 words, channel c in byte c (unused bytes 0).
 #pragma once
 #include <cstdint>
@@ -20,65 +20,52 @@ __device__ __forceinline__ uint32_t energy_at(const uint32_t *img, int pitch, in
   return sad4(row[jr], row[jl]) + sad4(img[(int64_t)id * pitch + j], img[(int64_t)iu * pitch + j]);
 }
 
-// The two energies of row i that the removal of `seam` changes. After deleting seam s from a
-// W-wide image, the energy of the (W-1)-wide image equals the old energy shifted left past s_i,
-// except at the new columns s_i - 1 and s_i (their left/right neighbour changed, and, since
-// |s_i - s_(i+-1)| <= 1, they are the only pixels whose upper/lower neighbour can change). They
-// are computed from the old image seen through the removal: new pixel (r, j) = old (r, j + [j >= s_r]).
-// Returns (e(s-1) | e(s) << 16); a value is 0 when its column does not exist. *bad is set when
-// the seam column is out of range.
-__device__ __forceinline__ uint32_t patch_row(const uint32_t *img, int pitch, int H, int W, const int32_t *seam,
-                                              int i, bool *bad) {
-  const int Wn = W - 1;
-  const int s = seam[i];
-  if (s < 0 || s >= W) {
-    *bad = true;
-    return 0u;
-  }
-  auto pix = [&](int r, int j) -> uint32_t {
-    r = clampi(r, 0, H - 1);
-    j = clampi(j, 0, Wn - 1);
-    const int sr = seam[r];
-    return img[(int64_t)r * pitch + j + (j >= sr ? 1 : 0)];
-  };
-  auto en = [&](int j) -> uint32_t { return sad4(pix(i, j + 1), pix(i, j - 1)) + sad4(pix(i + 1, j), pix(i - 1, j)); };
-  const uint32_t p0 = (s >= 1) ? en(s - 1) : 0u;
-  const uint32_t p1 = (s <= Wn - 1) ? en(s) : 0u;
-  return p0 | (p1 << 16);
-}
-
-// In-place left shift by one of row[s+1 .. W-1] -> row[s .. W-2] by one warp: left to right in
-// chunks of 32*R elements, every chunk read completely (by all lanes) before any lane writes it,
-// so no element is overwritten before it has been read.
-template <typename T>
-__device__ __forceinline__ void shift_row(T *row, int s, int W, int lane) {
-  constexpr int R = 8;
-  for (int base = s; base < W - 1; base += 32 * R) {
-    T x[R];
+// In-place left shift by one of a 16-byte-aligned uint16 row, row[s+1 .. W-1] -> row[s .. W-2],
+// by one warp, 8 elements (one 16-byte load and store) at a time: chunk c of the result is chunk c of the input moved down one element, with the first
+// element of chunk c+1 shifted in; every lane reads its chunks and the element after each chunk
+// before any lane of the warp writes. The first chunk keeps its elements left of s. Elements from
+// W-1 to the end of the last chunk are left undefined (they lie in the row's padding or in the
+// column that the shift drops).
+__device__ __forceinline__ void shift_row_u16(uint16_t *row, int s, int W, int lane) {
+  constexpr int R = 4;
+  if (s >= W - 1) return;
+  const int c_lo = s >> 3, c_hi = (W - 2) >> 3;
+  for (int cb = c_lo; cb <= c_hi; cb += 32 * R) {
+    uint4 x[R];
+    uint32_t nx[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int j = base + r * 32 + lane;
-      x[r] = (j + 1 < W) ? row[j + 1] : T(0);
+      const int c = cb + r * 32 + lane;
+      if (c <= c_hi) {
+        x[r] = *reinterpret_cast<const uint4 *>(row + 8 * c);
+        nx[r] = row[8 * c + 8];
+      }
     }
     __syncwarp();
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int j = base + r * 32 + lane;
-      if (j < W - 1) row[j] = x[r];
+      const int c = cb + r * 32 + lane;
+      if (c <= c_hi) {
+        uint4 o;
+        o.x = __funnelshift_r(x[r].x, x[r].y, 16);
+        o.y = __funnelshift_r(x[r].y, x[r].z, 16);
+        o.z = __funnelshift_r(x[r].z, x[r].w, 16);
+        o.w = __funnelshift_r(x[r].w, nx[r], 16);
+        if (c == c_lo) {
+          const int keep = s - 8 * c;   // leading elements of this chunk that stay
+          auto merge = [keep](uint32_t in, uint32_t sh, int q) {
+            const uint32_t m = (2 * q < keep ? 0x0000FFFFu : 0u) | (2 * q + 1 < keep ? 0xFFFF0000u : 0u);
+            return (in & m) | (sh & ~m);
+          };
+          o.x = merge(x[r].x, o.x, 0);
+          o.y = merge(x[r].y, o.y, 1);
+          o.z = merge(x[r].z, o.z, 2);
+          o.w = merge(x[r].w, o.w, 3);
+        }
+        *reinterpret_cast<uint4 *>(row + 8 * c) = o;
+      }
     }
     __syncwarp();
-  }
-}
-
-// Compaction of row i of the image words and of the energy, then the two refreshed energies.
-__device__ __forceinline__ void compact_row(uint32_t *img, int pitch, uint16_t *E, int pe, int W, int s,
-                                            uint32_t patch, int i, int lane) {
-  shift_row(img + (int64_t)i * pitch, s, W, lane);
-  uint16_t *er = E + (int64_t)i * pe;
-  shift_row(er, s, W, lane);
-  if (lane == 0) {
-    if (s >= 1) er[s - 1] = (uint16_t)(patch & 0xFFFFu);
-    if (s <= W - 2) er[s] = (uint16_t)(patch >> 16);
   }
 }
 
@@ -115,9 +102,14 @@ __device__ __forceinline__ int lazy_map(const int16_t *list, int m, int j) {
   return j + c;
 }
 
-// The two energies of row i that removing `seam` changes (as patch_row), with the image read
-// through the pending-removal lists `lists` (row r at lists + r*RPEND, m entries each) of the
-// width-W image the seam was found in.
+// The two energies of row i that the removal of `seam` changes. After deleting seam s from a
+// W-wide image, the energy of the (W-1)-wide image equals the old energy shifted left past s_i,
+// except at the new columns s_i - 1 and s_i (their left/right neighbour changed, and, since
+// |s_i - s_(i+-1)| <= 1, they are the only pixels whose upper/lower neighbour can change). They
+// are computed from the old image seen through the removal: new pixel (r, j) = old (r, j + [j >= s_r]).
+// Returns (e(s-1) | e(s) << 16); a value is 0 when its column does not exist. *bad is set when
+// the seam column is out of range. The image is read through the pending-removal lists `lists`
+// (row r at lists + r*RPEND, m entries each) of the width-W image the seam was found in.
 __device__ __forceinline__ uint32_t patch_row_lazy(const uint32_t *img, int pitch, int H, int W, const int32_t *seam,
                                                    const int16_t *lists, int m, int i, bool *bad) {
   const int Wn = W - 1;
@@ -201,7 +193,7 @@ __device__ __forceinline__ bool refresh_row(const uint32_t *img, int pitch, uint
   }
   p = __shfl_sync(0xffffffffu, p, 0);
   uint16_t *er = E + (int64_t)i * pe;
-  shift_row(er, s, W, lane);
+  shift_row_u16(er, s, W, lane);
   if (lane == 0) {
     if (s >= 1) er[s - 1] = (uint16_t)(p & 0xFFFFu);
     if (s <= W - 2) er[s] = (uint16_t)(p >> 16);

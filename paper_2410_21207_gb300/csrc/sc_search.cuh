@@ -405,7 +405,18 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   int32_t *const seam_out = p.seam;
   int32_t *const seam_log = p.seam_log;
   int *const errw = p.err;
+  // the energies of a super-tile's window (KS rows x FILL_W columns, two rows per lane) are
+  // prefetched into L2 one super-tile ahead: the map has usually left L2 since the DP pass read it
+  auto prefetch_window = [&](int s) {
+    if (s >= S) return;
+    int x0 = jb0[s] - 128;
+    x0 -= ((x0 % 8) + 8) % 8;
+    for (int i = s * KS + lane; i < s * KS + KS && i < H; i += 32)
+      bulk_prefetch_l2(Ef + (size_t)i * pitch_e + x0, FILL_W * 2);
+  };
+  if (ok && warp < G::FW) prefetch_window(warp * cs + rank);
   for (int s = warp * cs + rank; ok && warp < G::FW && s < S; s += G::FW * cs) {
+    prefetch_window(s + G::FW * cs);
     const int jbs = jb0[s];
     const int jprev = (s > 0) ? jb0[s - 1] : jb0[S];
     int x0 = jbs - 128;
