@@ -11,6 +11,7 @@
 
 #include "../../include/sc.h"
 #include "sc_batch_item.h"
+#include "sc_batch_cl.h"
 #include "sc_host.h"
 #include "sc_internal.cuh"
 #include "sc_rowops.cuh"
@@ -502,13 +503,50 @@ int batch_need_width(const sc_image_desc &d) {
 }
 
 
-// Lays out every batched image's scratch in one pool (offsets; `pool` may be null to size it).
+// Scratch of one image in the pool at `off` (pool may be null to size it). `limit` is the widest
+// column range the search stages: the CTA's width, or the cluster's owned columns.
+static BatchItem layout_item(const sc_image_desc &d, int limit, unsigned char *pool, size_t &off, int *S_out) {
+  const int nh = d.H - d.target_h;
+  const int R = d.H > d.W ? d.H : d.W;
+  const int rows_max = (nh > 0 && d.target_w > d.H) ? d.target_w : d.H;
+  const int cols_max = nh > 0 ? R : d.W;
+  BatchItem it;
+  it.img = d.img;
+  it.out = d.out;
+  it.seam_log = d.seam_log;
+  it.cost_log = nullptr;
+  it.H = d.H; it.W = d.W; it.C = d.C; it.tw = d.target_w; it.th = d.target_h;
+  it.pitch = round_up(R, 4);
+  // the search stages columns [-KT - 64, limit + 64) whatever the image width
+  it.pe = pitch_e_for(cols_max > limit + 64 ? cols_max : limit + 64);
+  it.pad = 0;
+  const int S = (rows_max + KS - 1) / KS;
+  *S_out = S;
+  auto take = [&](size_t bytes) { unsigned char *p = pool ? pool + off : nullptr; off += a256(bytes); return p; };
+  it.img_w = (uint32_t *)take((size_t)d.H * it.pitch * 4);
+  it.img2_w = nh > 0 ? (uint32_t *)take((size_t)d.target_w * it.pitch * 4) : nullptr;
+  it.E = (uint16_t *)take((size_t)rows_max * it.pe * 2);
+  it.Mrow = (uint32_t *)take((size_t)(S + 1) * it.pe * 4);
+  it.seam = (int32_t *)take((size_t)rows_max * 4);
+  it.lists = (int16_t *)take((size_t)2 * rows_max * RPEND * 2);
+  return it;
+}
+
+int batch_cluster_size(const sc_image_desc &d) {
+  const int own = batch_cl_own_cols();
+  return (batch_need_width(d) + own - 1) / own;
+}
+
+// Lays out every batched image's scratch in one pool (offsets; `pool` may be null to size it):
+// images that one CTA of configuration c covers first, then the wider ones by cluster size.
 void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned char *pool, BatchSetup &b) {
   b.items.clear();
+  b.cl.clear();
   b.fallback.clear();
   b.Smax = 1;
   size_t off = 0;
   const int limit = batch_width_limit(c.nw, c.kt);
+  std::vector<int> wide;
   for (int k = 0; k < n; ++k) {
     const sc_image_desc &d = descs[k];
     const int nh0 = d.H - d.target_h;
@@ -516,33 +554,32 @@ void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned
     // the refreshed pairs of a pass live in the CTA's staging ring between searches
     const size_t ring_bytes = (size_t)3 * c.kt * (c.nw * (128 - 2 * c.kt) + 2 * c.kt) * 2;
     if (batch_need_width(d) > limit || (size_t)rows0 * 4 > ring_bytes) {
+      wide.push_back(k);
+      continue;
+    }
+    int S;
+    b.items.push_back(layout_item(d, limit, pool, off, &S));
+    if (S > b.Smax) b.Smax = S;
+  }
+  for (int k : wide) {
+    const sc_image_desc &d = descs[k];
+    const int cs = batch_cluster_size(d);
+    if (cs > MAX_CLUSTER) {
       b.fallback.push_back(k);
       continue;
     }
-    const int nh = d.H - d.target_h;
-    const int R = d.H > d.W ? d.H : d.W;
-    const int rows_max = (nh > 0 && d.target_w > d.H) ? d.target_w : d.H;
-    const int cols_max = nh > 0 ? R : d.W;
-    BatchItem it;
-    it.img = d.img;
-    it.out = d.out;
-    it.seam_log = d.seam_log;
-    it.cost_log = nullptr;
-    it.H = d.H; it.W = d.W; it.C = d.C; it.tw = d.target_w; it.th = d.target_h;
-    it.pitch = round_up(R, 4);
-    // the single-CTA search stages columns [-KT, limit + KT) whatever the image width
-    it.pe = pitch_e_for(cols_max > limit + 64 ? cols_max : limit + 64);
-    it.pad = 0;
-    const int S = (rows_max + KS - 1) / KS;
-    if (S > b.Smax) b.Smax = S;
-    auto take = [&](size_t bytes) { unsigned char *p = pool ? pool + off : nullptr; off += a256(bytes); return p; };
-    it.img_w = (uint32_t *)take((size_t)d.H * it.pitch * 4);
-    it.img2_w = nh > 0 ? (uint32_t *)take((size_t)d.target_w * it.pitch * 4) : nullptr;
-    it.E = (uint16_t *)take((size_t)rows_max * it.pe * 2);
-    it.Mrow = (uint32_t *)take((size_t)(S + 1) * it.pe * 4);
-    it.seam = (int32_t *)take((size_t)rows_max * 4);
-    it.lists = (int16_t *)take((size_t)2 * rows_max * RPEND * 2);
-    b.items.push_back(it);
+    ClusterGroup *g = nullptr;
+    for (ClusterGroup &x : b.cl)
+      if (x.cs == cs) g = &x;
+    if (!g) {
+      b.cl.emplace_back();
+      g = &b.cl.back();
+      g->cs = cs;
+    }
+    int S;
+    g->items.push_back(layout_item(d, cs * batch_cl_own_cols(), pool, off, &S));
+    g->index.push_back(k);
+    if (S > g->Smax) g->Smax = S;
   }
   b.pool_bytes = off;
 }
@@ -573,11 +610,12 @@ static BatchCfg default_batch_cfg(const sc_image_desc *descs, int n) {
 
 struct BatchRun {
   DevBuf<unsigned char> pool;
-  DevBuf<BatchItem> items;
-  DevBuf<int> queue;
+  DevBuf<BatchItem> items;      // one-CTA images, then every cluster group's images
+  DevBuf<int> queue;            // one counter for the one-CTA launch and one per cluster group
   BatchSetup setup;
   BatchCfg cfg{15, 16};
   int grid = 1;
+  std::vector<int> cl_clusters;   // clusters launched per group
 };
 
 // Allocates and uploads everything one batched launch needs (synchronous upload).
@@ -587,9 +625,13 @@ static int batch_prepare(BatchRun &r, const sc_image_desc *descs, int n, const B
   SC_CUDA(r.pool.ensure(r.setup.pool_bytes ? r.setup.pool_bytes : 256));
   batch_layout(descs, n, c, r.pool.p, r.setup);
   const int nb = (int)r.setup.items.size();
-  SC_CUDA(r.items.ensure(nb ? nb : 1));
-  SC_CUDA(r.queue.ensure(1));
-  if (nb) SC_CUDA(cudaMemcpy(r.items.p, r.setup.items.data(), nb * sizeof(BatchItem), cudaMemcpyHostToDevice));
+  const int ng = (int)r.setup.cl.size();
+  std::vector<BatchItem> all = r.setup.items;
+  for (const ClusterGroup &g : r.setup.cl) all.insert(all.end(), g.items.begin(), g.items.end());
+  SC_CUDA(r.items.ensure(all.empty() ? 1 : all.size()));
+  SC_CUDA(r.queue.ensure((size_t)1 + ng));
+  if (!all.empty())
+    SC_CUDA(cudaMemcpy(r.items.p, all.data(), all.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
   int dev = 0, sms = 1;
   SC_CUDA(cudaGetDevice(&dev));
   SC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -597,17 +639,40 @@ static int batch_prepare(BatchRun &r, const sc_image_desc *descs, int n, const B
   r.grid = sms * per_sm;
   if (r.grid > nb) r.grid = nb;
   if (r.grid < 1) r.grid = 1;
+  r.cl_clusters.assign(ng, 1);
+  for (int g = 0; g < ng; ++g) {
+    int cap = 0;
+    SC_CUDA(batch_cl_capacity(r.setup.cl[g].cs, r.setup.cl[g].Smax, &cap));
+    const int ni = (int)r.setup.cl[g].items.size();
+    r.cl_clusters[g] = cap < 1 ? 1 : (cap < ni ? cap : ni);
+  }
   return SC_OK;
 }
 
-static int batch_enqueue(BatchRun &r, const sc_image_desc *descs, cudaStream_t st, int *err) {
+// the launches of one batched carve (what a plan captures)
+static cudaError_t batch_launches(BatchRun &r, cudaStream_t st, int *err) {
   const int nb = (int)r.setup.items.size();
+  const int ng = (int)r.setup.cl.size();
+  cudaError_t e = cudaMemsetAsync(r.queue.p, 0, (size_t)(1 + ng) * sizeof(int), st);
+  if (e != cudaSuccess) return e;
   if (nb) {
-    SC_CUDA(cudaMemsetAsync(r.queue.p, 0, sizeof(int), st));
-    SC_CUDA(timed("carve_batch", st, [&] {
-      return launch_batch(r.cfg.nw, r.cfg.kt, r.items.p, nb, r.setup.Smax, r.grid, r.queue.p, err, st);
-    }));
+    e = launch_batch(r.cfg.nw, r.cfg.kt, r.items.p, nb, r.setup.Smax, r.grid, r.queue.p, err, st);
+    if (e != cudaSuccess) return e;
   }
+  size_t base = nb;
+  for (int g = 0; g < ng; ++g) {
+    const ClusterGroup &G = r.setup.cl[g];
+    e = launch_batch_cl(r.items.p + base, (int)G.items.size(), G.cs, G.Smax, r.cl_clusters[g], r.queue.p + 1 + g,
+                        err, st);
+    if (e != cudaSuccess) return e;
+    base += G.items.size();
+  }
+  return cudaSuccess;
+}
+
+static int batch_enqueue(BatchRun &r, const sc_image_desc *descs, cudaStream_t st, int *err) {
+  if (!r.setup.items.empty() || !r.setup.cl.empty())
+    SC_CUDA(timed("carve_batch", st, [&] { return batch_launches(r, st, err); }));
   for (int k : r.setup.fallback) {
     const sc_image_desc &d = descs[k];
     int rc = carve_impl(d.img, d.H, d.W, d.C, d.target_w, d.target_h, d.out, d.seam_log, nullptr, st);
@@ -677,8 +742,6 @@ int sc_batch_plan_create(const sc_image_desc *descs, int n, int autotune, void *
       if (batch_smem_bytes(c.nw, c.kt, b.Smax) > 232448 - 1024) continue;
       BatchRun trial;
       if ((rc = batch_prepare(trial, descs, n, c))) { delete p; return rc; }
-      BatchSetup keep = trial.setup;
-      trial.setup.fallback.clear();   // time the batched launch alone
       if ((rc = batch_enqueue(trial, descs, st, p->err))) { delete p; return rc; }
       SC_CUDA(cudaEventRecord(e0, st));
       if ((rc = batch_enqueue(trial, descs, st, p->err))) { delete p; return rc; }
@@ -687,21 +750,18 @@ int sc_batch_plan_create(const sc_image_desc *descs, int n, int autotune, void *
       float ms = 0.f;
       SC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
       if (ms < best_ms) { best_ms = ms; best = c; }
-      trial.setup = keep;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
   }
   if ((rc = batch_prepare(p->run, descs, n, best))) { delete p; return rc; }
-  // capture the batched launch (queue reset + persistent kernel) in a CUDA graph
-  const int nb = (int)p->run.setup.items.size();
-  if (nb) {
+  // capture the batched launches (queue reset + persistent kernels) in a CUDA graph
+  if (!p->run.setup.items.empty() || !p->run.setup.cl.empty()) {
     cudaStream_t cap;
     SC_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     SC_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e1 = cudaMemsetAsync(p->run.queue.p, 0, sizeof(int), cap);
-    cudaError_t e2 = launch_batch(best.nw, best.kt, p->run.items.p, nb, p->run.setup.Smax, p->run.grid,
-                                  p->run.queue.p, p->err, cap);
+    cudaError_t e1 = cudaSuccess;
+    cudaError_t e2 = batch_launches(p->run, cap, p->err);
     cudaError_t e3 = cudaStreamEndCapture(cap, &p->graph);
     cudaStreamDestroy(cap);
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
@@ -733,7 +793,7 @@ int sc_batch_plan_info(const sc_batch_plan *plan, int *nw, int *kt, int *grid, i
   if (kt) *kt = plan->run.cfg.kt;
   if (grid) *grid = plan->run.grid;
   if (batched) *batched = (int)plan->run.setup.items.size();
-  if (fallback) *fallback = (int)plan->run.setup.fallback.size();
+  if (fallback) *fallback = plan->run.setup.cluster_images() + (int)plan->run.setup.fallback.size();
   return SC_OK;
 }
 

@@ -21,16 +21,32 @@ int *device_error_word();
 struct BatchCfg {
   int nw, kt;
 };
+// images wider than one CTA, carved by the cluster-per-image batched kernel (one group per
+// cluster size)
+struct ClusterGroup {
+  int cs = 1;
+  int Smax = 1;
+  std::vector<BatchItem> items;
+  std::vector<int> index;         // descriptor index of each item
+};
 struct BatchSetup {
-  std::vector<BatchItem> items;   // batched images (device pointers filled in)
-  std::vector<int> fallback;      // descriptor indices carved by the cluster path
+  std::vector<BatchItem> items;   // images carved by one CTA each (device pointers filled in)
+  std::vector<ClusterGroup> cl;   // images carved by one cluster each
+  std::vector<int> fallback;      // descriptor indices carved by the per-seam cluster path
   size_t pool_bytes = 0;
   int Smax = 1;
+  int cluster_images() const {
+    int n = 0;
+    for (const ClusterGroup &g : cl) n += (int)g.items.size();
+    return n;
+  }
 };
 inline size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // widest searched width of an image (its width, or its height when it has horizontal seams)
 int batch_need_width(const sc_image_desc &d);
 void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned char *pool, BatchSetup &b);
+// CTAs in the cluster that carves an image wider than one CTA
+int batch_cluster_size(const sc_image_desc &d);
 
 }  // namespace sc

@@ -81,3 +81,43 @@ def test_batch_plan_autotuned_replays(dev):
         for t, im in zip(d, imgs):
             t.copy_(torch.from_numpy(im))
     plan.close()
+
+
+def _wide_batch(rng):
+    """Images wider than any one-CTA configuration (cluster sizes 3 to 6 of the cluster kernel), a
+    tall one whose horizontal pass is the wide search, and two small ones in the same batch."""
+    shapes = [(64, 1800, 3, 40, 0), (40, 2600, 1, 30, 3), (90, 3300, 4, 25, 0), (120, 4096, 3, 20, 6),
+              (1700, 50, 3, 4, 30), (33, 200, 3, 10, 2), (70, 2100, 3, 35, 0), (16, 300, 1, 5, 0)]
+    imgs, targets = [], []
+    for k, (H, W, C, nv, nh) in enumerate(shapes):
+        if k % 3 == 1:
+            img = rng.integers(0, 3, size=(H, W, C)).astype(np.uint8)      # many exact ties
+        else:
+            img = rng.integers(0, 256, size=(H, W, C)).astype(np.uint8)
+        imgs.append(img)
+        targets.append((W - nv, H - nh))
+    return imgs, targets
+
+
+def test_batch_wide_images_cluster_kernel(dev):
+    rng = np.random.default_rng(77)
+    imgs, targets = _wide_batch(rng)
+    d = [torch.from_numpy(i).to(dev) for i in imgs]
+    outs, logs = sc.carve_batch(d, targets, with_log=True)
+    sc.check()
+    _check(imgs, targets, outs, logs)
+
+
+def test_batch_plan_with_wide_images_replays(dev):
+    """A plan whose graph holds the one-CTA launch and the cluster launches replays exactly."""
+    rng = np.random.default_rng(78)
+    imgs, targets = _wide_batch(rng)
+    d = [torch.from_numpy(i).to(dev) for i in imgs]
+    plan = sc.BatchPlan(d, targets, autotune=False, with_log=True)
+    info = plan.info()
+    assert info["batched"] + info["cluster_path"] == len(imgs) and info["cluster_path"] >= 5
+    for _ in range(2):
+        plan.run()
+        sc.check()
+        _check(imgs, targets, plan.outs, plan.logs)
+    plan.close()
