@@ -234,9 +234,12 @@ def serving_measurement(sc, torch, dev, imgs, n):
     reqs = synth.config5(n=n)
     seams = sum(r.seams for r in reqs)
     srv = sc.Server(budget_bytes=40 << 30, max_batch=64, streams=16)
-    w = srv.submit(imgs[0], reqs[0].target_w, reqs[0].target_h)
+    warm = [srv.submit(imgs[k], reqs[k].target_w, reqs[k].target_h) for k in range(min(n, 8))]
     srv.drain()
-    srv.release(w)
+    for t in warm:
+        srv.release(t)
+    st0 = srv.stats()
+    # (1) the trace's arrival times, replayed in real time: latency under the offered load
     tickets = []
     t0 = time.perf_counter()
     for k, r in enumerate(reqs):
@@ -248,6 +251,15 @@ def serving_measurement(sc, torch, dev, imgs, n):
     wall = time.perf_counter() - t0
     lats = [srv.poll(t)[1] for t in tickets]
     st = srv.stats()
+    for t in tickets:
+        srv.release(t)
+    # (2) every request submitted at once: the server's capacity (throughput when never idle)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(imgs[k], r.target_w, r.target_h) for k, r in enumerate(reqs)]
+    srv.drain(900)
+    cap_wall = time.perf_counter() - t0
+    for t in tickets:
+        srv.release(t)
     srv.close()
     # plain path: FIFO, one request at a time, per-seam launches
     dimgs = [torch.from_numpy(imgs[k]).to(dev) for k in range(n)]
@@ -267,13 +279,17 @@ def serving_measurement(sc, torch, dev, imgs, n):
     return {"workload": f"first {n} requests of the 10,000-request trace (seed 5): Poisson 200 req/s, "
                         "W, H log-uniform 128..4096 x 128..2160, target 50..90 % x 80..100 %",
             "served": {"req_per_s": n / wall, "seams_per_s": seams / wall, "p50_ms": 1e3 * _pct(lats, 0.5),
-                       "p99_ms": 1e3 * _pct(lats, 0.99), "launch_groups": st["groups"],
-                       "batched": st["batched"] - 1, "cluster_path": st["cluster_path"],
-                       "peak_device_bytes": st["peak_bytes"], "budget_bytes": st["budget_bytes"]},
+                       "p99_ms": 1e3 * _pct(lats, 0.99), "launch_groups": st["groups"] - st0["groups"],
+                       "one_cta_images": st["batched"] - st0["batched"],
+                       "cluster_images": st["cluster_path"] - st0["cluster_path"],
+                       "peak_device_bytes": st["peak_bytes"], "budget_bytes": st["budget_bytes"],
+                       "note": "arrivals replayed in real time; throughput is bounded by the offered load"},
+            "served_capacity": {"req_per_s": n / cap_wall, "seams_per_s": seams / cap_wall,
+                                "note": "the same requests submitted at once (host->device->host copies included)"},
             "plain": {"req_per_s": n / plain_busy, "seams_per_s": seams / plain_busy,
                       "p50_ms": 1e3 * _pct(plain_lat, 0.5), "p99_ms": 1e3 * _pct(plain_lat, 0.99),
                       "note": "same arrivals, first-come first-served, one request at a time"},
-            "served_over_plain_throughput": (seams / wall) / (seams / plain_busy)}
+            "served_over_plain_throughput": plain_busy / cap_wall}
 
 
 def fourk_measurement(sc, torch, dev, flush, steps):

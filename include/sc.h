@@ -184,13 +184,14 @@ typedef struct {
  * checks (nothing is enqueued then); device-side errors via sc_check. */
 int sc_carve_batch(const sc_image_desc *descs, int n, void *stream);
 
-/* A batch plan: the scratch, the descriptor table and a CUDA graph of the persistent launch,
- * built once and replayed. autotune != 0 times every tile height / warp-count configuration
- * (DP tile height 8, 16 or 32 rows; 8 or 15 compute warps per CTA) on the real batch and keeps
- * the fastest. The images' contents may change between runs; their pointers and sizes may not.
- * sc_batch_plan_run enqueues one replay on `stream`; sc_batch_plan_info reports the chosen
- * configuration (compute warps, tile height, CTAs launched, images batched / sent to the
- * cluster path). */
+/* A batch plan: the scratch, the descriptor table and a CUDA graph of the persistent launches,
+ * built once and replayed. Images that one CTA covers are carved by the one-CTA persistent
+ * kernel; wider ones by the cluster-per-image persistent kernel, one launch per cluster size.
+ * autotune != 0 times every one-CTA configuration (8, 12 or 15 compute warps per CTA; DP tile
+ * height 8, 16 or 32 rows) on the real batch and keeps the fastest. The images' contents may
+ * change between runs; their pointers and sizes may not. sc_batch_plan_run enqueues one replay on
+ * `stream`; sc_batch_plan_info reports the chosen configuration (compute warps, tile height, CTAs
+ * launched, images carved by one CTA / by one cluster each). */
 typedef struct sc_batch_plan sc_batch_plan;
 int sc_batch_plan_create(const sc_image_desc *descs, int n, int autotune, void *stream, sc_batch_plan **plan);
 int sc_batch_plan_run(sc_batch_plan *plan, void *stream);
@@ -198,13 +199,13 @@ int sc_batch_plan_info(const sc_batch_plan *plan, int *nw, int *kt, int *grid, i
 int sc_batch_plan_destroy(sc_batch_plan *plan);
 
 /* ---- serving form: continuous batching with device-memory admission ----
- * A server owns one device arena of budget_bytes (the memory ledger) and `streams` CUDA streams
- * (half carve micro-batches, half carve wide requests on the cluster path). A worker thread admits
- * queued requests in arrival order whenever the arena and a stream have room: requests that fit
- * one CTA (searched width <= 1440) are grouped, up to max_batch, into one persistent batched
- * launch; wider ones are carved alone by the cluster path. Groups on different streams run
- * concurrently, so requests submitted while others are on the GPU start as soon as memory and a
- * stream free up. Every result equals sc_carve of that image alone.
+ * A server owns one device arena of budget_bytes (the memory ledger) and `streams` CUDA streams.
+ * A worker thread admits queued requests whenever the arena and a stream have room, as
+ * micro-batches of up to max_batch requests of one kind, in arrival order within the kind:
+ * requests that fit one CTA (searched width <= 1440) go to one persistent one-CTA-per-image
+ * launch, wider ones to one persistent cluster-per-image launch per cluster size. Micro-batches
+ * on different streams run concurrently, so requests submitted while others are on the GPU start
+ * as soon as memory and a stream free up. Every result equals sc_carve of that image alone.
  * sc_server_submit: img_host (H*W*C bytes) and out_host (target_h*target_w*C bytes) are host
  *   buffers that must stay valid until the request completes; they should be pinned (page-locked),
  *   otherwise the device->host copy makes the worker wait for that group. Images up to 4096 x 4096.

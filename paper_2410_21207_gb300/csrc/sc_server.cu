@@ -3,14 +3,15 @@
 // Callers submit carve requests (host buffers) at any time. A worker thread repeatedly
 //   1. retires launch groups whose completion event has fired (frees their memory, time-stamps
 //      their requests),
-//   2. admits queued requests in arrival order while the device-memory ledger (one arena of the
-//      configured budget, first-fit) has room: requests that fit one CTA are gathered into a
-//      micro-batch (up to max_batch images) carved by one persistent k_batch launch; wider ones are
-//      carved alone by the cluster path,
-//   3. enqueues each group on a free stream: host->device copies, the carve, device->host copies,
-//      a completion event.
-// Groups on different streams run concurrently on the GPU, so requests that arrive while others
-// are being carved start as soon as memory and a stream are free, and their work overlaps.
+//   2. admits queued requests while the device-memory ledger (one arena of the configured budget,
+//      first-fit) has room, as micro-batches of up to max_batch requests of one kind, in arrival
+//      order within the kind: requests that fit one CTA go to the one-CTA persistent kernel
+//      (k_batch), wider ones to the cluster-per-image persistent kernel (k_batch_cl), one
+//      micro-batch per cluster size,
+//   3. enqueues each micro-batch on a free stream: host->device copies, the launch, device->host
+//      copies, a completion event.
+// Micro-batches on different streams run concurrently on the GPU, so requests that arrive while
+// others are being carved start as soon as memory and a stream are free, and their work overlaps.
 // Results do not depend on the grouping: every image is carved by the same integer arithmetic.
 #include <algorithm>
 #include <chrono>
@@ -22,12 +23,11 @@
 #include <unordered_map>
 #include <vector>
 
+#include "sc_batch_cl.h"
 #include "sc_host.h"
 #include "sc_internal.cuh"
 
 namespace sc {
-
-int workspace_reserve(cudaStream_t st, int H, int W);   // sc_api.cu
 
 namespace {
 
@@ -90,7 +90,7 @@ struct Request {
 };
 
 struct Group {
-  bool wide = false;                               // a single request on the cluster path
+  int cs = 0;                                      // 0: one-CTA micro-batch; else the cluster size
   std::vector<int64_t> tickets;
   std::vector<std::pair<size_t, size_t>> allocs;   // arena (offset, bytes)
   cudaStream_t stream = nullptr;
@@ -109,7 +109,8 @@ struct sc_server {
   sc::BatchCfg cfg{15, 16};
   int sms = 1, occ = 1;
   sc::Arena arena;
-  std::vector<cudaStream_t> batch_streams, big_streams;   // free pools
+  std::vector<cudaStream_t> streams;   // free pool
+  std::map<std::pair<int, int>, int> cl_capacity;   // (cluster size, super-tiles) -> clusters
   std::mutex mu;
   std::condition_variable cv;
   std::deque<int64_t> queue;
@@ -126,17 +127,24 @@ struct sc_server {
 namespace sc {
 namespace {
 
-size_t item_bytes(const sc_image_desc &d, const BatchCfg &c, int *Smax) {
-  BatchSetup b;
-  batch_layout(&d, 1, c, nullptr, b);
-  if (!b.items.empty()) *Smax = std::max(*Smax, b.Smax);
-  return b.pool_bytes;
-}
-
-bool fits_cta(const sc_server *s, const Request &r) {
+sc_image_desc desc_of(const Request &r) {
   sc_image_desc d{};
   d.H = r.H; d.W = r.W; d.C = r.C; d.target_w = r.tw; d.target_h = r.th;
-  return batch_need_width(d) <= batch_width_limit(s->cfg.nw, s->cfg.kt);
+  return d;
+}
+
+// 0 for a request one CTA carves, else the size of the cluster that carves it
+int kind_of(const sc_server *s, const Request &r) {
+  const sc_image_desc d = desc_of(r);
+  return batch_need_width(d) <= batch_width_limit(s->cfg.nw, s->cfg.kt) ? 0 : batch_cluster_size(d);
+}
+
+// scratch bytes and super-tiles of one request's carve
+size_t item_bytes(const sc_server *s, const sc_image_desc &d, int *S) {
+  BatchSetup b;
+  batch_layout(&d, 1, s->cfg, nullptr, b);
+  *S = b.items.empty() ? (b.cl.empty() ? 1 : b.cl[0].Smax) : b.Smax;
+  return b.pool_bytes;
 }
 
 // Retire finished groups (caller holds the lock).
@@ -158,53 +166,16 @@ void retire(sc_server *s) {
     for (auto &a : G.allocs) s->arena.release(a.first, a.second);
     cudaEventDestroy(G.done);
     cudaFreeHost(G.h_err);
-    if (G.wide)
-      s->big_streams.push_back(G.stream);
-    else
-      s->batch_streams.push_back(G.stream);
+    s->streams.push_back(G.stream);
     s->inflight.erase(s->inflight.begin() + g);
   }
   s->cv.notify_all();
 }
 
-// Start one group if possible (caller holds the lock). Returns true if something was launched.
+// Start one micro-batch if possible (caller holds the lock). Returns true if something was launched.
 bool admit(sc_server *s) {
-  if (s->queue.empty()) return false;
-  const int64_t head = s->queue.front();
-  Request &r0 = s->reqs[head];
-  if (!fits_cta(s, r0)) {
-    // a request wider than one CTA: alone, on the cluster path (its scratch is the stream's
-    // workspace, reserved at creation)
-    if (s->big_streams.empty()) return false;
-    const size_t nin = (size_t)r0.H * r0.W * r0.C, nout = (size_t)r0.th * r0.tw * r0.C;
-    size_t oin, oout, oerr;
-    if (!s->arena.alloc(nin, &oin)) return false;
-    if (!s->arena.alloc(nout, &oout)) { s->arena.release(oin, nin); return false; }
-    if (!s->arena.alloc(4, &oerr)) { s->arena.release(oin, nin); s->arena.release(oout, nout); return false; }
-    Group G;
-    G.wide = true;
-    G.stream = s->big_streams.back();
-    s->big_streams.pop_back();
-    G.tickets.push_back(head);
-    G.allocs = {{oin, nin}, {oout, nout}, {oerr, 4}};
-    cudaHostAlloc((void **)&G.h_err, sizeof(int), cudaHostAllocDefault);
-    *G.h_err = 0;
-    uint8_t *din = s->arena.base + oin, *dout = s->arena.base + oout;
-    cudaMemcpyAsync(din, r0.in, nin, cudaMemcpyHostToDevice, G.stream);
-    const int rc = carve_impl(din, r0.H, r0.W, r0.C, r0.tw, r0.th, dout, nullptr, nullptr, G.stream);
-    *G.h_err = rc ? 1 : 0;
-    cudaMemcpyAsync(r0.out, dout, nout, cudaMemcpyDeviceToHost, G.stream);
-    cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming);
-    cudaEventRecord(G.done, G.stream);
-    r0.status = 1;
-    s->queue.pop_front();
-    s->inflight.push_back(G);
-    s->big_count++;
-    s->groups++;
-    return true;
-  }
-  // a micro-batch of the queued requests that fit one CTA, in arrival order
-  if (s->batch_streams.empty()) return false;
+  if (s->queue.empty() || s->streams.empty()) return false;
+  const int kind = kind_of(s, s->reqs[s->queue.front()]);
   std::vector<int64_t> take;
   std::vector<sc_image_desc> descs;
   std::vector<std::pair<size_t, size_t>> allocs;
@@ -212,12 +183,13 @@ bool admit(sc_server *s) {
   for (int64_t tk : s->queue) {
     if ((int)take.size() >= s->max_batch) break;
     Request &r = s->reqs[tk];
-    if (!fits_cta(s, r)) break;   // keep arrival order: a wide request waits for its own turn
-    sc_image_desc d{};
-    d.H = r.H; d.W = r.W; d.C = r.C; d.target_w = r.tw; d.target_h = r.th;
-    int sm = Smax;
-    const size_t scratch = item_bytes(d, s->cfg, &sm);
-    if (batch_smem_bytes(s->cfg.nw, s->cfg.kt, sm) > 232448 - 1024) break;
+    if (kind_of(s, r) != kind) continue;   // another kind's micro-batch takes it
+    sc_image_desc d = desc_of(r);
+    int S = 1;
+    const size_t scratch = item_bytes(s, d, &S);
+    const int sm = std::max(Smax, S);
+    const size_t smem = kind ? batch_cl_smem_bytes(sm) : batch_smem_bytes(s->cfg.nw, s->cfg.kt, sm);
+    if (smem > 232448 - 1024) break;
     const size_t nin = (size_t)r.H * r.W * r.C, nout = (size_t)r.th * r.tw * r.C;
     size_t oin, oout, osc;
     if (!s->arena.alloc(nin, &oin)) break;
@@ -240,7 +212,12 @@ bool admit(sc_server *s) {
   const int n = (int)take.size();
   size_t otab, oq;
   const size_t tab_bytes = (size_t)n * sizeof(BatchItem);
-  if (!s->arena.alloc(tab_bytes, &otab) || !s->arena.alloc(256, &oq)) {
+  if (!s->arena.alloc(tab_bytes, &otab)) {
+    for (auto &a : allocs) s->arena.release(a.first, a.second);
+    return false;
+  }
+  if (!s->arena.alloc(256, &oq)) {
+    s->arena.release(otab, tab_bytes);
     for (auto &a : allocs) s->arena.release(a.first, a.second);
     return false;
   }
@@ -251,11 +228,12 @@ bool admit(sc_server *s) {
   for (int k = 0; k < n; ++k) {
     BatchSetup b;
     batch_layout(&descs[k], 1, s->cfg, s->arena.base + allocs[3 * k + 2].first, b);
-    items[k] = b.items[0];
+    items[k] = kind ? b.cl[0].items[0] : b.items[0];
   }
   Group G;
-  G.stream = s->batch_streams.back();
-  s->batch_streams.pop_back();
+  G.cs = kind;
+  G.stream = s->streams.back();
+  s->streams.pop_back();
   G.tickets = take;
   G.allocs = allocs;
   cudaHostAlloc((void **)&G.h_err, sizeof(int), cudaHostAllocDefault);
@@ -270,9 +248,21 @@ bool admit(sc_server *s) {
     cudaMemcpyAsync((void *)descs[k].img, r.in, (size_t)r.H * r.W * r.C, cudaMemcpyHostToDevice, G.stream);
     r.status = 1;
   }
-  int grid = s->sms * s->occ;
-  if (grid > n) grid = n;
-  const cudaError_t le = launch_batch(s->cfg.nw, s->cfg.kt, dtab, n, Smax, grid, q, derr, G.stream);
+  cudaError_t le;
+  if (kind) {
+    auto key = std::make_pair(kind, Smax);
+    auto it = s->cl_capacity.find(key);
+    if (it == s->cl_capacity.end()) {
+      int cap = 0;
+      if (batch_cl_capacity(kind, Smax, &cap) != cudaSuccess || cap < 1) cap = 1;
+      it = s->cl_capacity.emplace(key, cap).first;
+    }
+    le = launch_batch_cl(dtab, n, kind, Smax, std::min(n, it->second), q, derr, G.stream);
+  } else {
+    int grid = s->sms * s->occ;
+    if (grid > n) grid = n;
+    le = launch_batch(s->cfg.nw, s->cfg.kt, dtab, n, Smax, grid, q, derr, G.stream);
+  }
   if (le != cudaSuccess) *G.h_err = 1;
   for (int k = 0; k < n; ++k) {
     Request &r = s->reqs[take[k]];
@@ -281,9 +271,12 @@ bool admit(sc_server *s) {
   cudaMemcpyAsync(G.h_err, derr, sizeof(int), cudaMemcpyDeviceToHost, G.stream);
   cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming);
   cudaEventRecord(G.done, G.stream);
-  for (int k = 0; k < n; ++k) s->queue.pop_front();
+  for (int64_t tk : take) s->queue.erase(std::find(s->queue.begin(), s->queue.end(), tk));
   s->inflight.push_back(G);
-  s->batched_count += n;
+  if (kind)
+    s->big_count += n;
+  else
+    s->batched_count += n;
   s->groups++;
   return true;
 }
@@ -334,17 +327,7 @@ int sc_server_create(size_t budget_bytes, int max_batch, int streams, sc_server 
       delete s;
       return fail(SC_ECUDA, "stream creation failed");
     }
-    // half the streams carve micro-batches, half carve wide requests on the cluster path
-    if (k % 2 == 0) {
-      s->batch_streams.push_back(st);
-    } else {
-      const int rc = workspace_reserve(st, 4096, 4096);   // no allocation while serving
-      if (rc) {
-        delete s;
-        return rc;
-      }
-      s->big_streams.push_back(st);
-    }
+    s->streams.push_back(st);
   }
   s->worker = std::thread(worker_loop, s);
   *out = s;
@@ -362,13 +345,8 @@ int sc_server_submit(sc_server *s, const uint8_t *img_host, int H, int W, int C,
   r.out = out_host;
   r.H = H; r.W = W; r.C = C; r.tw = target_w; r.th = target_h;
   r.t_submit = now_s();
-  size_t need = (size_t)H * W * C + (size_t)target_h * target_w * C + 1024;
-  if (fits_cta(s, r)) {
-    sc_image_desc d{};
-    d.H = H; d.W = W; d.C = C; d.target_w = target_w; d.target_h = target_h;
-    int sm = 1;
-    need += item_bytes(d, s->cfg, &sm) + 4096;
-  }
+  int S = 1;
+  const size_t need = (size_t)H * W * C + (size_t)target_h * target_w * C + item_bytes(s, desc_of(r), &S) + 4096;
   if (need > s->arena.size) return fail(SC_ENOMEM, "a %d x %d request needs more than the whole budget", W, H);
   std::lock_guard<std::mutex> lk(s->mu);
   const int64_t t = s->next_ticket++;
@@ -433,8 +411,7 @@ int sc_server_destroy(sc_server *s) {
     s->cv.notify_all();
   }
   if (s->worker.joinable()) s->worker.join();
-  for (cudaStream_t st : s->batch_streams) cudaStreamDestroy(st);
-  for (cudaStream_t st : s->big_streams) cudaStreamDestroy(st);
+  for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   if (s->arena.base) cudaFree(s->arena.base);
   delete s;
   return SC_OK;
