@@ -32,6 +32,7 @@
 // The result is Algorithm 3's seam exactly (leftmost ties, leftmost last-row minimum).
 #pragma once
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "sc_internal.cuh"
 #include "sc_ptx.cuh"
@@ -255,102 +256,110 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
         bulk_g2s(ring + (size_t)(slot * KT + lane) * BW, Estage + (size_t)(rbeg + lane) * pitch_e, ROW_BYTES,
                  &full[slot]);
     }
+  } else if (!active) {
+    // outside the image: release every slot at once and keep the barrier count
+    for (int t = 0; t < nt; ++t) {
+      const uint32_t g = st.tiles + t;
+      if (lane == 0) mbar_arrive(&empty[g % NSLOT]);
+      if (t * KT + KT < H) named_bar_sync(NW * 32);
+    }
   } else {
     uint32_t k[V] = {0u, 0u, 0u, 0u};
-    for (int t = 0; t < nt; ++t) {
-      const int r0 = t * KT;
-      const bool more = r0 + KT < H;
-      const uint32_t g = st.tiles + t;
-      const int slot = (int)(g % NSLOT);
-      if (!active) {
-        // outside the image: release the slot at once and keep the barrier count
-        if (lane == 0) mbar_arrive(&empty[slot]);
-        if (more) named_bar_sync(NW * 32);
-        continue;
-      }
-      if (!mbar_wait_bounded(&full[slot], (g / NSLOT) & 1u, WAIT_TIMEOUT_NS)) {
-        if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
-      }
-      const uint16_t *er = ring + (size_t)slot * KT * BW + bidx0;
-      if (t > 0) {
-        // window of the previous row from the boundary buffer (relative ancestors -> warp frame)
-        const uint4 v = *reinterpret_cast<const uint4 *>(bnd + ((t - 1) & 1) * BW + bidx0);
-        if (r0 % KS == 0) {
-          // a new super-tile: every cell becomes its own ancestor. The old ancestor field is
-          // dropped without arithmetic: it may lie outside this warp's frame.
-          const uint32_t a = (uint32_t)(c0 - frame_base);
-          k[0] = (v.x & ~0xFFu) | a; k[1] = (v.y & ~0xFFu) | (a + 1);
-          k[2] = (v.z & ~0xFFu) | (a + 2); k[3] = (v.w & ~0xFFu) | (a + 3);
+    // The tile loop, compiled twice: EDGE warps hold columns outside the image and apply the
+    // exclusion mask on every row; the others never test it.
+    auto tiles = [&](auto edge_tag) {
+      constexpr bool EDGE = decltype(edge_tag)::value;
+      const uint32_t own_a = (uint32_t)(c0 - frame_base);   // this lane's first column, warp frame
+      bool ready = false;                                    // next tile's rows already tested staged
+      for (int t = 0; t < nt; ++t) {
+        const int r0 = t * KT;
+        const bool more = r0 + KT < H;
+        const uint32_t g = st.tiles + t;
+        const int slot = (int)(g % NSLOT);
+        if (!ready && !mbar_wait_bounded(&full[slot], (g / NSLOT) & 1u, WAIT_TIMEOUT_NS)) {
+          if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
+        }
+        // test the next tile's staging now: the answer is needed only at the next tile boundary
+        ready = more && mbar_test_wait(&full[(g + 1) % NSLOT], ((g + 1) / NSLOT) & 1u);
+        const uint16_t *er = ring + (size_t)slot * KT * BW + bidx0;
+        if (t > 0) {
+          // window of the previous row from the boundary buffer (relative ancestors -> warp frame).
+          // At a new super-tile every cell becomes its own ancestor; the old ancestor field is
+          // dropped without arithmetic (it may lie outside this warp's frame).
+          const uint4 v = *reinterpret_cast<const uint4 *>(bnd + ((t - 1) & 1) * BW + bidx0);
+          const bool fresh = (r0 % KS) == 0;
+          const uint32_t d = own_a - 128u;
+          k[0] = fresh ? ((v.x & ~0xFFu) | own_a) : (v.x + d);
+          k[1] = fresh ? ((v.y & ~0xFFu) | (own_a + 1u)) : (v.y + d + 1u);
+          k[2] = fresh ? ((v.z & ~0xFFu) | (own_a + 2u)) : (v.z + d + 2u);
+          k[3] = fresh ? ((v.w & ~0xFFu) | (own_a + 3u)) : (v.w + d + 3u);
+          if (EDGE) { k[0] |= oobm[0]; k[1] |= oobm[1]; k[2] |= oobm[2]; k[3] |= oobm[3]; }
+        }
+        if (t > 0 && r0 + KT <= H) {
+          // full tile: KT branch-free rows (the energies of the next rows are loaded ahead of
+          // the row that needs them, off the dependent chain); bookkeeping only where a
+          // super-tile or the image ends on its last row
+          dp_rows<KT, BW, EDGE>(k, er, oobm);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[slot]);   // this warp is done with the staged rows
+          if (((r0 + KT) % KS) == 0 || r0 + KT == H)
+            row_events(r0 + KT - 1, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, lastmin);
         } else {
-          // relative ancestor -> this warp's frame (exact for every cell that can reach the strip)
-          const uint32_t d = (uint32_t)(c0 - frame_base) - 128u;
-          k[0] = v.x + d; k[1] = v.y + d + 1u; k[2] = v.z + d + 2u; k[3] = v.w + d + 3u;
-        }
-        k[0] |= oobm[0]; k[1] |= oobm[1]; k[2] |= oobm[2]; k[3] |= oobm[3];
-      }
-      if (t > 0 && !(r0 + KT > H)) {
-        // full tile: KT branch-free rows, bookkeeping only on its last row. The energies of the
-        // next rows are loaded ahead of the row that needs them, off the dependent chain; only
-        // warps that hold columns outside the image apply the exclusion mask.
-        if (edge) dp_rows<KT, BW, true>(k, er, oobm);
-        else dp_rows<KT, BW, false>(k, er, oobm);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[slot]);   // this warp is done with the staged rows
-        row_events(r0 + KT - 1, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, lastmin);
-      } else {
-        // first tile (row 0 has no predecessor) or a ragged last tile
-        for (int r = 0; r < KT; ++r) {
-          const int i = r0 + r;
-          if (i >= H) break;
-          const uint2 ev = *reinterpret_cast<const uint2 *>(er + r * BW);
-          if (i == 0) {
-            const uint32_t a = (uint32_t)(c0 - frame_base);
-            k[0] = (lo8(ev.x) | a) | oobm[0];
-            k[1] = (hi8(ev.x) | (a + 1)) | oobm[1];
-            k[2] = (lo8(ev.y) | (a + 2)) | oobm[2];
-            k[3] = (hi8(ev.y) | (a + 3)) | oobm[3];
-          } else {
-            dp_row(k, ev, oobm);
-          }
-          row_events(i, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, lastmin);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[slot]);
-      }
-      if (more) {
-        const bool exch = CL && ((r0 + KT) % K2 == 0) && cs > 1;
-        const uint32_t d = (uint32_t)(c0 - frame_base) - 128u;
-        uint4 v;
-        v.x = k[0] - d; v.y = k[1] - d - 1u; v.z = k[2] - d - 2u; v.w = k[3] - d - 3u;
-        // publish this warp's strip (relative ancestor encoding); at an exchange the CTA's halo
-        // columns come from the neighbours instead
-        if (strip_lane && (!exch || (c0 >= A && c0 < B)))
-          *reinterpret_cast<uint4 *>(bnd + (t & 1) * BW + bidx0) = v;
-        if (CL && exch) {
-          const uint32_t xg = st.exch + (uint32_t)((r0 + KT) / K2 - 1);
-          const int par = (int)(xg & 1);
-          // my first K2 own columns are the left neighbour's right halo, my last K2 the right's left
-          if (strip_lane && rank > 0 && c0 >= A && c0 < A + K2)
-            st_async_v4(mapa_u32(hbuf + par * 2 * K2 + K2 + (c0 - A), rank - 1), v, mapa_u32(&hbar[par], rank - 1));
-          if (strip_lane && rank < cs - 1 && c0 >= B - K2 && c0 < B)
-            st_async_v4(mapa_u32(hbuf + par * 2 * K2 + (c0 - (B - K2)), rank + 1), v, mapa_u32(&hbar[par], rank + 1));
-          if (threadIdx.x == 0)
-            mbar_arrive_expect_tx(&hbar[par], (uint32_t)(((rank > 0) + (rank < cs - 1)) * K2 * 4));
-          if (!mbar_wait_bounded(&hbar[par], (xg >> 1) & 1u, WAIT_TIMEOUT_NS)) {
-            if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
-          }
-          uint32_t *mine = bnd + (t & 1) * BW;
-          for (int q = threadIdx.x; q < 2 * K2; q += NW * 32) {
-            if (q < K2) {
-              if (rank > 0) mine[(A - K2 + q) - (ext0 - KT)] = hbuf[par * 2 * K2 + q];
+          // first tile (row 0 has no predecessor) or a ragged last tile
+          for (int r = 0; r < KT; ++r) {
+            const int i = r0 + r;
+            if (i >= H) break;
+            const uint2 ev = *reinterpret_cast<const uint2 *>(er + r * BW);
+            if (i == 0) {
+              k[0] = (lo8(ev.x) | own_a) | oobm[0];
+              k[1] = (hi8(ev.x) | (own_a + 1u)) | oobm[1];
+              k[2] = (lo8(ev.y) | (own_a + 2u)) | oobm[2];
+              k[3] = (hi8(ev.y) | (own_a + 3u)) | oobm[3];
             } else {
-              if (rank < cs - 1) mine[(B + (q - K2)) - (ext0 - KT)] = hbuf[par * 2 * K2 + q];
+              dp_row(k, ev, oobm);
+            }
+            row_events(i, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, lastmin);
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[slot]);
+        }
+        if (more) {
+          const bool exch = CL && ((r0 + KT) % K2 == 0) && cs > 1;
+          const uint32_t d = own_a - 128u;
+          uint4 v;
+          v.x = k[0] - d; v.y = k[1] - d - 1u; v.z = k[2] - d - 2u; v.w = k[3] - d - 3u;
+          // publish this warp's strip (relative ancestor encoding); at an exchange the CTA's halo
+          // columns come from the neighbours instead
+          if (strip_lane && (!exch || (c0 >= A && c0 < B)))
+            *reinterpret_cast<uint4 *>(bnd + (t & 1) * BW + bidx0) = v;
+          if (CL && exch) {
+            const uint32_t xg = st.exch + (uint32_t)((r0 + KT) / K2 - 1);
+            const int par = (int)(xg & 1);
+            // my first K2 own columns are the left neighbour's right halo, my last K2 the right's left
+            if (strip_lane && rank > 0 && c0 >= A && c0 < A + K2)
+              st_async_v4(mapa_u32(hbuf + par * 2 * K2 + K2 + (c0 - A), rank - 1), v, mapa_u32(&hbar[par], rank - 1));
+            if (strip_lane && rank < cs - 1 && c0 >= B - K2 && c0 < B)
+              st_async_v4(mapa_u32(hbuf + par * 2 * K2 + (c0 - (B - K2)), rank + 1), v, mapa_u32(&hbar[par], rank + 1));
+            if (threadIdx.x == 0)
+              mbar_arrive_expect_tx(&hbar[par], (uint32_t)(((rank > 0) + (rank < cs - 1)) * K2 * 4));
+            if (!mbar_wait_bounded(&hbar[par], (xg >> 1) & 1u, WAIT_TIMEOUT_NS)) {
+              if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
+            }
+            uint32_t *mine = bnd + (t & 1) * BW;
+            for (int q = threadIdx.x; q < 2 * K2; q += NW * 32) {
+              if (q < K2) {
+                if (rank > 0) mine[(A - K2 + q) - (ext0 - KT)] = hbuf[par * 2 * K2 + q];
+              } else {
+                if (rank < cs - 1) mine[(B + (q - K2)) - (ext0 - KT)] = hbuf[par * 2 * K2 + q];
+              }
             }
           }
+          named_bar_sync(NW * 32);
         }
-        named_bar_sync(NW * 32);
       }
-    }
+    };
+    if (edge) tiles(std::integral_constant<bool, true>());
+    else tiles(std::integral_constant<bool, false>());
   }
   st.tiles += (uint32_t)nt;
   if (CL && nt > 0) st.exch += (uint32_t)((cs > 1) ? ((H - 1) / K2) : 0);
