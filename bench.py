@@ -65,9 +65,9 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _traffic_from_profile():
-    """Per-launch DRAM bytes of the DP kernel from the committed ncu summary, if any."""
-    path = os.path.join(ROOT, "profiles", "k_dp_1920x1080.txt")
+def _traffic_from_profile(name="k_dp_1920x1080.txt"):
+    """Per-launch DRAM bytes of a kernel from its committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
             for ln in f:
@@ -354,6 +354,7 @@ def uhd_search_measurement(sc, torch, dev, steps, peak):
             "kernel": "k_dp_multi", "kernel_us_per_launch": 1e6 * tk,
             "algorithmic_bytes_per_launch": alg, "achieved_gbs": alg / tk / 1e9,
             "peak_gbs": peak, "frac": alg / tk / 1e9 / peak if peak else None,
+            "traffic": _traffic_from_profile("k_dp_multi_3840x2160x58.txt") if B == 58 else None,
             "note": "working set B x 16.6 MB exceeds L2, so no flush; the call also copies each map into "
                     "its padded workspace (one extra kernel per map), the kernel figure excludes that"}
 
