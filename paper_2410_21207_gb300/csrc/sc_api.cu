@@ -1,5 +1,6 @@
 // C ABI of libsc_gb300 (declared in include/sc.h): argument checks, the per-(device, stream)
 // workspace, and the host-side seam loops of the plain path.
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -582,6 +583,26 @@ void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned
     if (S > g->Smax) g->Smax = S;
   }
   b.pool_bytes = off;
+  // the queues hand out the longest carves first (longest-processing-time order), so that no
+  // CTA starts a long image after the others have run dry
+  auto work = [](const BatchItem &it) {
+    return (double)(it.W - it.tw) * it.H * it.W + (double)(it.H - it.th) * it.tw * it.H;
+  };
+  auto by_work = [&](const BatchItem &a, const BatchItem &c) { return work(a) > work(c); };
+  std::stable_sort(b.items.begin(), b.items.end(), by_work);
+  for (ClusterGroup &g : b.cl) {
+    std::vector<int> order(g.items.size());
+    for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return by_work(g.items[x], g.items[y]); });
+    std::vector<BatchItem> items;
+    std::vector<int> index;
+    for (int q : order) {
+      items.push_back(g.items[q]);
+      index.push_back(g.index[q]);
+    }
+    g.items.swap(items);
+    g.index.swap(index);
+  }
 }
 
 static int check_batch_descs(const sc_image_desc *descs, int n) {

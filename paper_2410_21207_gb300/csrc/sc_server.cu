@@ -230,6 +230,11 @@ bool admit(sc_server *s) {
     batch_layout(&descs[k], 1, s->cfg, s->arena.base + allocs[3 * k + 2].first, b);
     items[k] = kind ? b.cl[0].items[0] : b.items[0];
   }
+  // longest carves first in the launch's queue
+  std::stable_sort(items.begin(), items.end(), [](const BatchItem &a, const BatchItem &c) {
+    return (double)(a.W - a.tw) * a.H * a.W + (double)(a.H - a.th) * a.tw * a.H >
+           (double)(c.W - c.tw) * c.H * c.W + (double)(c.H - c.th) * c.tw * c.H;
+  });
   Group G;
   G.cs = kind;
   G.stream = s->streams.back();
