@@ -207,9 +207,12 @@ int sc_batch_plan_destroy(sc_batch_plan *plan);
  * on different streams run concurrently, so requests submitted while others are on the GPU start
  * as soon as memory and a stream free up. Every result equals sc_carve of that image alone.
  * sc_server_submit: img_host (H*W*C bytes) and out_host (target_h*target_w*C bytes) are host
- *   buffers that must stay valid until the request completes; they should be pinned (page-locked),
- *   otherwise the device->host copy makes the worker wait for that group. Images up to 4096 x 4096.
- *   Returns a ticket. Errors: SC_EINVAL (as sc_carve), SC_ENOMEM (larger than the whole budget).
+ *   buffers that must stay valid until the request completes. The kernels write the carved image
+ *   into out_host directly when it is page-locked (cudaHostAlloc / cudaHostRegister), otherwise
+ *   into a page-locked staging block that the worker copies out; img_host should be page-locked
+ *   too (its host->device copy is then asynchronous). A request completes as soon as its own
+ *   image is done, whatever else its micro-batch holds. Images up to 4096 x 4096. Returns a
+ *   ticket. Errors: SC_EINVAL (as sc_carve), SC_ENOMEM (larger than the whole budget).
  * sc_server_poll: 1 when done (latency_s = completion - submission, seconds), 0 while pending,
  *   a negative status if the request failed.
  * sc_server_drain: waits until nothing is queued or running (SC_ETIMEOUT after timeout_s).

@@ -356,14 +356,17 @@ class Server:
         self._h = h
         self._keep = {}
 
-    def submit(self, img: np.ndarray, target_w: int, target_h: int) -> int:
+    def submit(self, img: np.ndarray, target_w: int, target_h: int, pinned: bool = True) -> int:
+        """Queue a carve; with pinned=False the buffers stay pageable (the server stages them)."""
         torch = self.torch
         a = np.ascontiguousarray(img, dtype=np.uint8)
         if a.ndim == 2:
             a = a[:, :, None]
         H, W, C = a.shape
-        src = torch.from_numpy(a).pin_memory()
-        dst = torch.empty((target_h, target_w, C), dtype=torch.uint8).pin_memory()
+        src = torch.from_numpy(a)
+        dst = torch.empty((target_h, target_w, C), dtype=torch.uint8)
+        if pinned:
+            src, dst = src.pin_memory(), dst.pin_memory()
         t = ctypes.c_int64(0)
         _raise(load().sc_server_submit(self._h, ctypes.c_void_p(src.data_ptr()), H, W, C, int(target_w),
                                        int(target_h), ctypes.c_void_p(dst.data_ptr()), ctypes.byref(t)))

@@ -521,6 +521,7 @@ static BatchItem layout_item(const sc_image_desc &d, int limit, unsigned char *p
   // the search stages columns [-KT - 64, limit + 64) whatever the image width
   it.pe = pitch_e_for(cols_max > limit + 64 ? cols_max : limit + 64);
   it.pad = 0;
+  it.done = nullptr;
   const int S = (rows_max + KS - 1) / KS;
   *S_out = S;
   auto take = [&](size_t bytes) { unsigned char *p = pool ? pool + off : nullptr; off += a256(bytes); return p; };

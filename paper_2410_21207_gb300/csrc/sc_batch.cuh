@@ -143,7 +143,9 @@ __device__ void batch_carve_item(const BatchItem &it, unsigned char *smem, int S
     const int i = (int)(q / tw), j = (int)(q % tw);
     unpack_pixel(res[(int64_t)i * it.pitch + j], it.out + q * C, C);
   }
+  if (it.done) __threadfence_system();   // every thread's output bytes before the completion word
   __syncthreads();
+  if (it.done && threadIdx.x == 0) *(volatile int *)it.done = (*(volatile int *)err != 0) ? 2 : 1;
 }
 
 template <int NW, int KT>

@@ -151,7 +151,9 @@ __device__ void clb_carve_item(const BatchItem &it, unsigned char *smem, int Sma
     const int i = (int)(q / tw), j = (int)(q % tw);
     unpack_pixel(it.img_w[(int64_t)i * it.pitch + j], it.out + q * C, C);
   }
+  if (it.done) __threadfence_system();   // every thread's output bytes before the completion word
   cg::this_cluster().sync();
+  if (it.done && rank == 0 && threadIdx.x == 0) *(volatile int *)it.done = (*(volatile int *)err != 0) ? 2 : 1;
 }
 
 __global__ void __launch_bounds__(GeoB::THREADS, 1)

@@ -20,6 +20,9 @@ struct BatchItem {
   uint32_t *Mrow;       // (ceil(rows/KS) + 1) x pe saved cost rows (column 0 at Mrow + E_PADL)
   int32_t *seam;        // rows
   int16_t *lists;       // two generations of pending-removal lists, rows x RPEND each
+  // nullable: set to 1 (or 2 if the device error word was non-zero) once `out` is complete and
+  // visible to the host; `out` may then be host-mapped memory (the serving form)
+  int *done;
 };
 
 // width a CTA of nw compute warps with tile height kt covers

@@ -8,12 +8,18 @@
 //      order within the kind: requests that fit one CTA go to the one-CTA persistent kernel
 //      (k_batch), wider ones to the cluster-per-image persistent kernel (k_batch_cl), one
 //      micro-batch per cluster size,
-//   3. enqueues each micro-batch on a free stream: host->device copies, the launch, device->host
-//      copies, a completion event.
+//   3. enqueues each micro-batch on a free stream: host->device copies of the inputs, the launch,
+//      a completion event.
+// The kernels write every carved image straight into host memory (the caller's page-locked output
+// buffer, or a page-locked staging block for pageable ones) and then set that image's completion
+// word in page-locked memory, so a request completes as soon as its own image is done, not when
+// its whole micro-batch is; its device memory is returned to the ledger at that moment.
 // Micro-batches on different streams run concurrently on the GPU, so requests that arrive while
 // others are being carved start as soon as memory and a stream are free, and their work overlaps.
 // Results do not depend on the grouping: every image is carved by the same integer arithmetic.
 #include <algorithm>
+#include <atomic>
+#include <cstring>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -35,9 +41,11 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// first-fit sub-allocator over one device region (256-byte granules)
+// first-fit sub-allocator over one device region, or one page-locked host region mapped into the
+// device's address space (256-byte granules)
 struct Arena {
   unsigned char *base = nullptr;
+  bool host = false;
   size_t size = 0, in_use = 0, peak = 0;
   std::map<size_t, size_t> free_;   // offset -> bytes
   bool init(size_t bytes) {
@@ -45,6 +53,20 @@ struct Arena {
     if (cudaMalloc(&base, size) != cudaSuccess) return false;
     free_[0] = size;
     return true;
+  }
+  bool init_host(size_t bytes) {
+    size = a256(bytes);
+    if (cudaHostAlloc((void **)&base, size, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+      base = nullptr;
+      return false;
+    }
+    host = true;
+    free_[0] = size;
+    return true;
+  }
+  void destroy() {
+    if (base) host ? cudaFreeHost(base) : cudaFree(base);
+    base = nullptr;
   }
   bool alloc(size_t n, size_t *off) {
     n = a256(n ? n : 1);
@@ -86,16 +108,22 @@ struct Request {
   uint8_t *out = nullptr;
   int H = 0, W = 0, C = 0, tw = 0, th = 0;
   double t_submit = 0, t_done = -1;
-  int status = 0;   // 0 queued, 1 on the GPU, 2 done, < 0 error
+  int status = 0;                                   // 0 queued, 1 on the GPU, 2 done, < 0 error
+  uint8_t *dout = nullptr;                          // where the kernel writes the result (host memory)
+  bool staged = false;                              // out is pageable: the result goes through staging
+  size_t hoff = 0, hbytes = 0;                      // staging block
+  int flag = -1;                                    // index of the completion word
+  std::vector<std::pair<size_t, size_t>> dallocs;   // device arena blocks (offset, bytes)
 };
 
 struct Group {
   int cs = 0;                                      // 0: one-CTA micro-batch; else the cluster size
   std::vector<int64_t> tickets;
-  std::vector<std::pair<size_t, size_t>> allocs;   // arena (offset, bytes)
+  std::vector<std::pair<size_t, size_t>> allocs;   // device arena blocks of the launch itself
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  int *h_err = nullptr;                            // pinned copy of the group's device error word
+  int err_slot = -1;                               // completion word receiving the device error word
+  int launch_failed = 0;
 };
 
 }  // namespace
@@ -109,6 +137,11 @@ struct sc_server {
   sc::BatchCfg cfg{15, 16};
   int sms = 1, occ = 1;
   sc::Arena arena;
+  sc::Arena staging;                   // page-locked results of pageable output buffers (lazy)
+  int *flags = nullptr;                // page-locked completion words, one per request on the GPU
+  std::vector<int> free_flags;
+  std::vector<cudaEvent_t> free_events;
+  std::vector<cudaEvent_t> all_events;
   std::vector<cudaStream_t> streams;   // free pool
   std::map<std::pair<int, int>, int> cl_capacity;   // (cluster size, super-tiles) -> clusters
   std::mutex mu;
@@ -147,25 +180,53 @@ size_t item_bytes(const sc_server *s, const sc_image_desc &d, int *S) {
   return b.pool_bytes;
 }
 
-// Retire finished groups (caller holds the lock).
+void release_request(sc_server *s, Request &r) {
+  for (auto &a : r.dallocs) s->arena.release(a.first, a.second);
+  r.dallocs.clear();
+  if (r.staged && r.hbytes) s->staging.release(r.hoff, r.hbytes);
+  r.hbytes = 0;
+  if (r.flag >= 0) s->free_flags.push_back(r.flag);
+  r.flag = -1;
+}
+
+void finish_request(sc_server *s, Request &r, bool ok, double t) {
+  if (ok && r.staged) std::memcpy(r.out, r.dout, (size_t)r.th * r.tw * r.C);
+  release_request(s, r);
+  r.t_done = t;
+  r.status = ok ? 2 : SC_EINTERNAL;
+  s->latencies.push_back(t - r.t_submit);
+  s->done_count++;
+  if (!ok) s->device_errors++;
+}
+
+// Retire every request whose image is complete, and every launch whose stream has finished
+// (caller holds the lock).
 void retire(sc_server *s) {
   const double t = now_s();
   for (size_t g = 0; g < s->inflight.size();) {
     Group &G = s->inflight[g];
-    const cudaError_t q = cudaEventQuery(G.done);
-    if (q == cudaErrorNotReady) { ++g; continue; }
-    const bool ok = (q == cudaSuccess) && (*G.h_err == 0);
-    if (!ok) s->device_errors++;
     for (int64_t tk : G.tickets) {
       Request &r = s->reqs[tk];
-      r.t_done = t;
-      r.status = ok ? 2 : SC_EINTERNAL;
-      s->latencies.push_back(t - r.t_submit);
-      s->done_count++;
+      if (r.status != 1) continue;
+      const int v = *(volatile int *)&s->flags[r.flag];
+      if (v == 0) continue;
+      std::atomic_thread_fence(std::memory_order_acquire);   // the result bytes after the word
+      finish_request(s, r, v == 1, t);
+    }
+    const cudaError_t q = cudaEventQuery(G.done);
+    if (q == cudaErrorNotReady) { ++g; continue; }
+    const bool ok = (q == cudaSuccess) && !G.launch_failed && (*(volatile int *)&s->flags[G.err_slot] == 0);
+    for (int64_t tk : G.tickets) {
+      Request &r = s->reqs[tk];
+      if (r.status != 1) continue;
+      const int v = *(volatile int *)&s->flags[r.flag];
+      std::atomic_thread_fence(std::memory_order_acquire);
+      finish_request(s, r, ok && v == 1, t);   // a launch that ended without completing it failed
     }
     for (auto &a : G.allocs) s->arena.release(a.first, a.second);
-    cudaEventDestroy(G.done);
-    cudaFreeHost(G.h_err);
+    s->free_events.push_back(G.done);   // page-locked allocations and frees would synchronise the
+    s->free_flags.push_back(G.err_slot);  // device: events and words come from pools
+
     s->streams.push_back(G.stream);
     s->inflight.erase(s->inflight.begin() + g);
   }
@@ -174,7 +235,7 @@ void retire(sc_server *s) {
 
 // Start one micro-batch if possible (caller holds the lock). Returns true if something was launched.
 bool admit(sc_server *s) {
-  if (s->queue.empty() || s->streams.empty()) return false;
+  if (s->queue.empty() || s->streams.empty() || s->free_events.empty() || s->free_flags.size() < 2) return false;
   const int kind = kind_of(s, s->reqs[s->queue.front()]);
   std::vector<int64_t> take;
   std::vector<sc_image_desc> descs;
@@ -191,45 +252,57 @@ bool admit(sc_server *s) {
     const size_t smem = kind ? batch_cl_smem_bytes(sm) : batch_smem_bytes(s->cfg.nw, s->cfg.kt, sm);
     if (smem > 232448 - 1024) break;
     const size_t nin = (size_t)r.H * r.W * r.C, nout = (size_t)r.th * r.tw * r.C;
-    size_t oin, oout, osc;
+    if (s->free_flags.size() < 2) break;   // one word stays for the launch's error word
+    if (r.staged && !s->staging.base && !s->staging.init_host(std::min(s->budget, (size_t)2 << 30))) break;
+    size_t oin, osc, ohost = 0;
     if (!s->arena.alloc(nin, &oin)) break;
-    if (!s->arena.alloc(nout, &oout)) { s->arena.release(oin, nin); break; }
-    if (!s->arena.alloc(scratch, &osc)) { s->arena.release(oin, nin); s->arena.release(oout, nout); break; }
+    if (!s->arena.alloc(scratch, &osc)) { s->arena.release(oin, nin); break; }
+    if (r.staged && !s->staging.alloc(nout, &ohost)) { s->arena.release(oin, nin); s->arena.release(osc, scratch); break; }
+    r.dallocs = {{oin, nin}, {osc, scratch}};
     allocs.push_back({oin, nin});
-    allocs.push_back({oout, nout});
     allocs.push_back({osc, scratch});
+    if (r.staged) {
+      r.hoff = ohost;
+      r.hbytes = nout;
+      r.dout = s->staging.base + ohost;
+    }
+    r.flag = s->free_flags.back();
+    s->free_flags.pop_back();
+    s->flags[r.flag] = 0;
     d.img = s->arena.base + oin;
-    d.out = s->arena.base + oout;
+    d.out = r.dout;
     d.seam_log = nullptr;
     descs.push_back(d);
     take.push_back(tk);
     Smax = sm;
   }
-  if (take.empty()) {
-    for (auto &a : allocs) s->arena.release(a.first, a.second);
-    return false;
-  }
+  auto undo = [&]() {
+    for (int64_t tk : take) release_request(s, s->reqs[tk]);
+  };
+  if (take.empty()) return false;
   const int n = (int)take.size();
   size_t otab, oq;
   const size_t tab_bytes = (size_t)n * sizeof(BatchItem);
   if (!s->arena.alloc(tab_bytes, &otab)) {
-    for (auto &a : allocs) s->arena.release(a.first, a.second);
+    undo();
     return false;
   }
   if (!s->arena.alloc(256, &oq)) {
     s->arena.release(otab, tab_bytes);
-    for (auto &a : allocs) s->arena.release(a.first, a.second);
+    undo();
     return false;
   }
-  allocs.push_back({otab, tab_bytes});
-  allocs.push_back({oq, 256});
   // per-image scratch layouts, each placed in its own arena block
   std::vector<BatchItem> items(n);
   for (int k = 0; k < n; ++k) {
     BatchSetup b;
-    batch_layout(&descs[k], 1, s->cfg, s->arena.base + allocs[3 * k + 2].first, b);
+    batch_layout(&descs[k], 1, s->cfg, s->arena.base + allocs[2 * k + 1].first, b);
     items[k] = kind ? b.cl[0].items[0] : b.items[0];
+    items[k].done = s->flags + s->reqs[take[k]].flag;   // page-locked, mapped: the same address on the device
   }
+  allocs.clear();
+  allocs.push_back({otab, tab_bytes});
+  allocs.push_back({oq, 256});
   // longest carves first in the launch's queue
   std::stable_sort(items.begin(), items.end(), [](const BatchItem &a, const BatchItem &c) {
     return (double)(a.W - a.tw) * a.H * a.W + (double)(a.H - a.th) * a.tw * a.H >
@@ -241,8 +314,9 @@ bool admit(sc_server *s) {
   s->streams.pop_back();
   G.tickets = take;
   G.allocs = allocs;
-  cudaHostAlloc((void **)&G.h_err, sizeof(int), cudaHostAllocDefault);
-  *G.h_err = 0;
+  G.err_slot = s->free_flags.back();
+  s->free_flags.pop_back();
+  s->flags[G.err_slot] = 0;
   int *q = reinterpret_cast<int *>(s->arena.base + oq);
   int *derr = q + 1;
   BatchItem *dtab = reinterpret_cast<BatchItem *>(s->arena.base + otab);
@@ -268,13 +342,10 @@ bool admit(sc_server *s) {
     if (grid > n) grid = n;
     le = launch_batch(s->cfg.nw, s->cfg.kt, dtab, n, Smax, grid, q, derr, G.stream);
   }
-  if (le != cudaSuccess) *G.h_err = 1;
-  for (int k = 0; k < n; ++k) {
-    Request &r = s->reqs[take[k]];
-    cudaMemcpyAsync(r.out, descs[k].out, (size_t)r.th * r.tw * r.C, cudaMemcpyDeviceToHost, G.stream);
-  }
-  cudaMemcpyAsync(G.h_err, derr, sizeof(int), cudaMemcpyDeviceToHost, G.stream);
-  cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming);
+  if (le != cudaSuccess) G.launch_failed = 1;
+  cudaMemcpyAsync(&s->flags[G.err_slot], derr, sizeof(int), cudaMemcpyDeviceToHost, G.stream);
+  G.done = s->free_events.back();
+  s->free_events.pop_back();
   cudaEventRecord(G.done, G.stream);
   for (int64_t tk : take) s->queue.erase(std::find(s->queue.begin(), s->queue.end(), tk));
   s->inflight.push_back(G);
@@ -325,6 +396,15 @@ int sc_server_create(size_t budget_bytes, int max_batch, int streams, sc_server 
     delete s;
     return fail(SC_ENOMEM, "cannot allocate the %zu-byte device arena", budget_bytes);
   }
+  constexpr int kFlags = 1 << 16;   // requests on the GPU at once
+  if (cudaHostAlloc((void **)&s->flags, kFlags * sizeof(int), cudaHostAllocMapped | cudaHostAllocPortable) !=
+      cudaSuccess) {
+    s->flags = nullptr;
+    s->arena.destroy();
+    delete s;
+    return fail(SC_ENOMEM, "cannot allocate the completion words");
+  }
+  for (int k = kFlags - 1; k >= 0; --k) s->free_flags.push_back(k);
   s->occ = batch_blocks_per_sm(s->cfg.nw, s->cfg.kt, 1);
   for (int k = 0; k < streams; ++k) {
     cudaStream_t st;
@@ -333,6 +413,13 @@ int sc_server_create(size_t budget_bytes, int max_batch, int streams, sc_server 
       return fail(SC_ECUDA, "stream creation failed");
     }
     s->streams.push_back(st);
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      delete s;
+      return fail(SC_ECUDA, "event creation failed");
+    }
+    s->free_events.push_back(ev);
+    s->all_events.push_back(ev);
   }
   s->worker = std::thread(worker_loop, s);
   *out = s;
@@ -349,6 +436,14 @@ int sc_server_submit(sc_server *s, const uint8_t *img_host, int H, int W, int C,
   r.in = img_host;
   r.out = out_host;
   r.H = H; r.W = W; r.C = C; r.tw = target_w; r.th = target_h;
+  // a page-locked output buffer is written by the kernels directly; a pageable one through staging
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, out_host) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+    r.dout = static_cast<uint8_t *>(pa.devicePointer);
+  } else {
+    cudaGetLastError();
+    r.staged = true;
+  }
   r.t_submit = now_s();
   int S = 1;
   const size_t need = (size_t)H * W * C + (size_t)target_h * target_w * C + item_bytes(s, desc_of(r), &S) + 4096;
@@ -417,7 +512,10 @@ int sc_server_destroy(sc_server *s) {
   }
   if (s->worker.joinable()) s->worker.join();
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
-  if (s->arena.base) cudaFree(s->arena.base);
+  for (cudaEvent_t ev : s->all_events) cudaEventDestroy(ev);
+  s->arena.destroy();
+  s->staging.destroy();
+  if (s->flags) cudaFreeHost(s->flags);
   delete s;
   return SC_OK;
 }

@@ -40,7 +40,7 @@ def test_served_results_equal_alone(dev):
     srv = sc.Server(budget_bytes=1 << 30, max_batch=8, streams=6)
     tickets = []
     for k, (img, tw, th) in enumerate(reqs):
-        tickets.append(srv.submit(img, tw, th))
+        tickets.append(srv.submit(img, tw, th, pinned=(k % 3 != 1)))   # some pageable buffers
         if k % 5 == 0:
             time.sleep(0.002)   # later requests arrive while earlier ones are on the GPU
     srv.drain(300)
@@ -73,4 +73,23 @@ def test_admission_waits_for_memory(dev):
         np.testing.assert_array_equal(srv.result(t), oracle.carve(img, tw, th))
     with pytest.raises(sc.ScError):
         srv.submit(np.zeros((4000, 4000, 3), dtype=np.uint8), 3000, 4000)   # larger than the budget
+    srv.close()
+
+
+def test_request_completes_with_its_own_image(dev):
+    """Small images batched with a long one complete long before it (per-image completion)."""
+    big = synth.gen_image(1300, 900, 3, 6, 200, 71)
+    smalls = [synth.gen_image(60 + 7 * k, 40 + 3 * k, 3, 2, 20, 80 + k) for k in range(6)]
+    srv = sc.Server(budget_bytes=1 << 30, max_batch=16, streams=2)
+    tb = srv.submit(big, 700, 900)
+    ts = [srv.submit(im, im.shape[1] - 10, im.shape[0]) for im in smalls]
+    srv.drain(300)
+    st = srv.stats()
+    assert st["completed"] == 7 and st["device_errors"] == 0
+    _, lat_big = srv.poll(tb)
+    lat_small = [srv.poll(t)[1] for t in ts]
+    assert max(lat_small) < 0.5 * lat_big, (lat_small, lat_big)
+    np.testing.assert_array_equal(srv.result(tb), oracle.carve(big, 700, 900))
+    for im, t in zip(smalls, ts):
+        np.testing.assert_array_equal(srv.result(t), oracle.carve(im, im.shape[1] - 10, im.shape[0]))
     srv.close()
