@@ -4,33 +4,34 @@
 
 namespace sc {
 
-using GeoC4 = Geo<4, DP_KT, true>;
-using GeoC8 = Geo<8, DP_KT, true>;
+// The search of one map is a chain of H dependent rows, so its shape is chosen for latency: tall
+// 32-row tiles cross a tile boundary (strip exchange, staging barrier, bookkeeping) half as often
+// as 16-row ones, at the price of more redundant halo columns, which only costs idle SMs. Shapes
+// in order of preference; the first whose cluster covers W is used.
+struct DpShapeDef {
+  int nw, kt, ow;
+};
+constexpr DpShapeDef kDpShapes[] = {
+    {4, 32, Geo<4, 32, true>::OWC}, {8, 32, Geo<8, 32, true>::OWC}, {8, 16, Geo<8, 16, true>::OWC}};
 
 DpShape dp_shape_for(int W) {
-  DpShape s;
-  s.nw = 4;
-  s.ow = GeoC4::OWC;
-  s.cs = (W + s.ow - 1) / s.ow;
-  if (s.cs > MAX_CLUSTER) {
-    s.nw = 8;
-    s.ow = GeoC8::OWC;
-    s.cs = (W + s.ow - 1) / s.ow;
+  DpShape s{};
+  for (const DpShapeDef &d : kDpShapes) {
+    s.nw = d.nw;
+    s.kt = d.kt;
+    s.ow = d.ow;
+    s.cs = (W + d.ow - 1) / d.ow;
+    if (s.cs < 1) s.cs = 1;
+    if (s.cs <= MAX_CLUSTER) break;
   }
-  if (s.cs < 1) s.cs = 1;
   return s;
 }
 
-size_t dp_smem_bytes(int nw, int H) {
-  const int S = (H + KS - 1) / KS;
-  return nw == 4 ? search_plan<4, DP_KT, true>(S).total : search_plan<8, DP_KT, true>(S).total;
-}
-
-template <int NW>
-__global__ void __launch_bounds__(Geo<NW, DP_KT, true>::THREADS, 1) k_dp(DpArgs p) {
+template <int NW, int KT>
+__global__ void __launch_bounds__(Geo<NW, KT, true>::THREADS, 1) k_dp(DpArgs p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int S = (p.H + KS - 1) / KS;
-  search_init<NW, DP_KT, true>(smem, S);
+  search_init<NW, KT, true>(smem, S);
   // neighbours push into each other's halo buffers: every CTA's barriers must be initialised first
   cg::this_cluster().sync();
   SearchArgs a;
@@ -45,24 +46,24 @@ __global__ void __launch_bounds__(Geo<NW, DP_KT, true>::THREADS, 1) k_dp(DpArgs 
   a.err = p.err;
   a.gated = (p.gate != nullptr) && (*p.gate & ERR_ENERGY_RANGE);
   SearchState st;
-  seam_search<NW, DP_KT, true>(a, smem, S, st);
+  seam_search<NW, KT, true>(a, smem, S, st);
 }
 
-template <int NW>
-static cudaError_t launch_dp_nw(const DpArgs &a, int cs, cudaStream_t st) {
-  const size_t smem = dp_smem_bytes(NW, a.H);
+template <int NW, int KT>
+static cudaError_t launch_dp_shape(const DpArgs &a, int cs, cudaStream_t st) {
+  const size_t smem = search_plan<NW, KT, true>((a.H + KS - 1) / KS).total;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_dp<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaError_t e = cudaFuncSetAttribute(k_dp<NW, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_dp<NW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(k_dp<NW, KT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   if (smem > 232448) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cs);
-  cfg.blockDim = dim3(Geo<NW, DP_KT, true>::THREADS);
+  cfg.blockDim = dim3(Geo<NW, KT, true>::THREADS);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
@@ -72,13 +73,15 @@ static cudaError_t launch_dp_nw(const DpArgs &a, int cs, cudaStream_t st) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_dp<NW>, a);
+  return cudaLaunchKernelEx(&cfg, k_dp<NW, KT>, a);
 }
 
 cudaError_t launch_dp(const DpArgs &a, cudaStream_t st) {
   const DpShape s = dp_shape_for(a.W);
   if (s.cs > MAX_CLUSTER) return cudaErrorInvalidValue;
-  return s.nw == 4 ? launch_dp_nw<4>(a, s.cs, st) : launch_dp_nw<8>(a, s.cs, st);
+  if (s.nw == 4 && s.kt == 32) return launch_dp_shape<4, 32>(a, s.cs, st);
+  if (s.nw == 8 && s.kt == 32) return launch_dp_shape<8, 32>(a, s.cs, st);
+  return launch_dp_shape<8, 16>(a, s.cs, st);
 }
 
 }  // namespace sc

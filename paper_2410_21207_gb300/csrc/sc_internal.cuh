@@ -20,11 +20,10 @@ constexpr int E_PADR = 1024;   // right pad (elements)
 // Seam-search geometry (sc_search.cuh). A lane owns V consecutive columns; a warp's window is
 // 32*V columns, of which 32*V - 2*KT are its own strip; windows exchange boundary rows every KT
 // rows inside a CTA (shared memory) and every K2 rows between the CTAs of a cluster (DSMEM).
-// Ancestors are tracked over super-tiles of KS rows. The cluster path uses KT = DP_KT.
+// Ancestors are tracked over super-tiles of KS rows. KT is a template parameter of each kernel.
 constexpr int V = 4;
 constexpr int KS = 64;
 constexpr int K2 = 64;
-constexpr int DP_KT = 16;
 constexpr int MAX_CLUSTER = 16;
 
 // Error bits recorded on the device.
@@ -38,12 +37,12 @@ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 inline int pitch_e_for(int W) { return E_PADL + round_up(W, 8) + E_PADR; }
 
 struct DpShape {
-  int nw;    // warps per CTA (4 or 8)
+  int nw;    // compute warps per CTA
+  int kt;    // DP tile rows
   int cs;    // CTAs in the cluster
   int ow;    // CTA-own columns = nw*Q - 2*K2
 };
 DpShape dp_shape_for(int W);
-size_t dp_smem_bytes(int nw, int H);
 
 struct DpArgs {
   const uint16_t *E;   // row 0, column 0 (already offset by E_PADL)
