@@ -42,6 +42,7 @@ def _args():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (256-image) measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (Poisson trace) measurement")
     ap.add_argument("--no-4k", action="store_true", help="skip the 3840x2160 measurement")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper's n x n workload points")
     ap.add_argument("--serving-requests", type=int, default=300)
     ap.add_argument("--profile-search", metavar="HxW[xB]", default=None,
                     help="only call sc_find_seam a few times on a seeded HxW energy map, or sc_find_seam_multi "
@@ -359,6 +360,65 @@ def uhd_search_measurement(sc, torch, dev, steps, peak):
                     "its padded workspace (one extra kernel per map), the kernel figure excludes that"}
 
 
+def paper_workload_measurement(sc, torch, dev, cpu: bool):
+    """The paper's own workload ("Runtime For different sized images"): n x n images at n = 180,
+    360, 480, 720, 1080 with s = 0.5, i.e. n/2 vertical seams. On the GPU: one DP seam search
+    T(n, n) (sc_find_seam), one greedy seam (sc_greedy_seam, Algorithm 2) and the full DP carve
+    C(n, n, 0.5) (sc_carve); on one host core, the oracle's DP seam, greedy seam and full carve, and
+    brute force (Algorithm 1) at n = 2, 5, 7, 10, 12 (the paper's brute-force sizes)."""
+    import numpy as np
+    from paper_2410_21207_gb300 import synth
+    import oracle
+
+    def ev_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    def cpu_s(fn, budget_s=1.0):
+        t0 = time.perf_counter()
+        fn()
+        t = time.perf_counter() - t0
+        reps = max(1, min(20, int(budget_s / max(t, 1e-6))))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        return (time.perf_counter() - t0) / reps
+
+    rows = []
+    for n in (180, 360, 480, 720, 1080):
+        R, smin, smax = synth.scaled_rects(n, n)
+        img = synth.gen_image(n, n, R, smin, smax, 7000 + n)
+        dimg = torch.from_numpy(img).to(dev)
+        e = sc.energy(dimg)
+        row = {"n": n, "seams": n // 2,
+               "gpu_dp_seam_ms": ev_ms(lambda: sc.find_seam(e), 20),
+               "gpu_greedy_seam_ms": ev_ms(lambda: sc.greedy_seam(e), 20),
+               "gpu_dp_carve_ms": ev_ms(lambda: sc.carve(dimg, n - n // 2, n), 3)}
+        if cpu:
+            e_host = oracle.energy(img)
+            row["cpu_dp_seam_ms"] = 1e3 * cpu_s(lambda: oracle.dp_seam(e_host))
+            row["cpu_greedy_seam_ms"] = 1e3 * cpu_s(lambda: oracle.greedy_seam(e_host))
+            row["cpu_dp_carve_ms"] = 1e3 * cpu_s(lambda: oracle.carve(img, n - n // 2, n), 0.0)
+        rows.append(row)
+    sc.check()
+    out = {"workload": "n x n synthetic images (generator G), s = 0.5: n/2 vertical seams", "points": rows}
+    if cpu:
+        rng = np.random.default_rng(425)
+        out["cpu_brute_force_seam_ms"] = {
+            str(n): 1e3 * cpu_s(lambda e=rng.integers(0, 1531, size=(n, n)).astype(np.uint16): oracle.brute_seam(e), 0.2)
+            for n in (2, 5, 7, 10, 12)}
+        out["cpu_cores"] = 1
+    return out
+
+
 def profile_search(spec: str):
     """sc_find_seam four times on a seeded H x W uint16 energy map (the kernel to capture is k_dp);
     with HxWxB, sc_find_seam_multi on B shifted copies (the kernel is k_dp_multi)."""
@@ -530,6 +590,8 @@ def run_native(a):
         line["uhd_3840x2160"] = fourk_measurement(sc, torch, dev, flush, a.steps)
     if rank == 0 and not a.no_4k:
         line["uhd_search_concurrent"] = uhd_search_measurement(sc, torch, dev, a.steps, peak)
+    if rank == 0 and not a.no_paper:
+        line["paper_nxn"] = paper_workload_measurement(sc, torch, dev, cpu=not a.no_cpu_baseline and ws == 1)
     if rank == 0 and serving_imgs is not None:
         line["serving"] = serving_measurement(sc, torch, dev, serving_imgs, a.serving_requests)
     if rank == 0 and not a.no_cpu_baseline and ws == 1:

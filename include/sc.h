@@ -96,6 +96,15 @@ int sc_energy(const uint8_t *img, int H, int W, int C, uint16_t *energy_out, voi
  *         or energies that could overflow (checked on the device: SC_EINTERNAL via sc_check). */
 int sc_find_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_t *cost_out, void *stream);
 
+/* ---- Algorithm 2 (section "Greedy Seam Carving"): the greedy seam ----
+ * Starts at the leftmost minimum of the bottom row and climbs, row by row, to the leftmost minimum
+ * of the in-range upper neighbours (j-1, j, j+1); cost = the sum of the energies on the seam.
+ * Not optimal in general (the DP seam's cost is a lower bound); the paper compares it with the DP.
+ * energy: device uint16 H x W row-major; seam_out: device int32[H]; cost_out: device int64 or
+ * NULL. Asynchronous on `stream`. Errors: SC_EINVAL for a null pointer or a shape outside
+ * 1..SC_MAX_ROWS x 1..SC_MAX_COLS. */
+int sc_greedy_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_t *cost_out, void *stream);
+
 /* ---- the same search for n independent maps of one size, in one launch ----
  * The Algorithm 3 seam (DP fill, last-row argmin, backtrack) of each map, independently.
  * energies: HOST array of n DEVICE pointers, each H x W uint16 row-major (as sc_find_seam).

@@ -63,6 +63,7 @@ def load(path: Optional[str] = None):
                 "sc_find_seam": ([P, I, I, P, P, P], I),
                 "sc_find_seam_static": ([P, I, I, P, P, P], I),
                 "sc_find_seam_multi": ([P, I, I, I, P, P, P], I),
+                "sc_greedy_seam": ([P, I, I, P, P, P], I),
                 "sc_find_seam_multi_capacity": ([I, I, P], I),
                 "sc_find_seam_multi_shape": ([I, I], I),
                 "sc_carve": ([P, I, I, I, I, I, P, P, P, P], I),
@@ -147,6 +148,18 @@ def find_seam(e):
     seam = torch.empty(H, dtype=torch.int32, device=e.device)
     cost = torch.empty(1, dtype=torch.int64, device=e.device)
     _raise(load().sc_find_seam(_ptr(e), H, W, _ptr(seam), _ptr(cost), _stream(torch, e.device)))
+    return seam, cost
+
+
+def greedy_seam(e):
+    """Algorithm 2's greedy seam of an H x W uint16 CUDA energy map -> (int32[H] seam, int64[1] cost)."""
+    torch = _torch()
+    if e.device.type != "cuda" or e.dtype != torch.uint16 or e.dim() != 2 or not e.is_contiguous():
+        raise ValueError("energy must be a contiguous H x W uint16 CUDA tensor")
+    H, W = e.shape
+    seam = torch.empty(H, dtype=torch.int32, device=e.device)
+    cost = torch.empty(1, dtype=torch.int64, device=e.device)
+    _raise(load().sc_greedy_seam(_ptr(e), H, W, _ptr(seam), _ptr(cost), _stream(torch, e.device)))
     return seam, cost
 
 

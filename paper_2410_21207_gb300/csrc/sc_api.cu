@@ -442,6 +442,14 @@ int sc_find_seam_multi(const uint16_t *const *energies, int n, int H, int W, int
   return SC_OK;
 }
 
+int sc_greedy_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_t *cost_out, void *stream) {
+  if (!energy || !seam_out) return fail(SC_EINVAL, "null pointer");
+  if (H < 1 || W < 1 || H > SC_MAX_ROWS || W > SC_MAX_COLS) return fail(SC_EINVAL, "bad shape %d x %d", H, W);
+  SC_CUDA(timed("greedy", (cudaStream_t)stream,
+                [&] { return launch_greedy(energy, H, W, seam_out, cost_out, (cudaStream_t)stream); }));
+  return SC_OK;
+}
+
 int sc_find_seam_multi_capacity(int H, int W, int *n_out) {
   if (!n_out) return fail(SC_EINVAL, "null pointer");
   if (H < 1 || W < 1 || H > SC_MAX_ROWS || W > SC_MAX_COLS) return fail(SC_EINVAL, "bad shape %d x %d", H, W);

@@ -74,6 +74,8 @@ cudaError_t dp_multi_capacity(int H, int W, int *n_out);
 // tile shape of launch_dp_multi: (compute warps per CTA, tile rows), (0, 0) = automatic;
 // returns -1 for a shape that is not built
 int dp_multi_set_shape(int nw, int kt);
+// Algorithm 2's greedy seam of an unpadded H x W map (one warp)
+cudaError_t launch_greedy(const uint16_t *e, int H, int W, int32_t *seam, int64_t *cost, cudaStream_t st);
 // lazy image compaction (sc_rowops.cuh): refresh + list update per seam, bulk compaction
 cudaError_t launch_compact_lazy(uint32_t *img, int pitch, int H, int w, const int16_t *lists, int m, cudaStream_t st);
 // per seam: refreshed pair through the lazy map, list update and energy compaction (one warp per row)

@@ -159,3 +159,80 @@ cudaError_t launch_compact_lazy(uint32_t *img, int pitch, int H, int w, const in
 }
 
 }  // namespace sc
+
+namespace sc {
+
+// ---- Algorithm 2 (greedy): start at the leftmost minimum of the bottom row, climb by the
+// leftmost minimum of the (in-range) upper neighbours. One warp per map: the bottom-row argmin is a
+// warp reduction; the climb is serial, so the warp stages the 65-column window it can reach in
+// the next 32 rows into shared memory and lane 0 walks it. ----
+constexpr int GREEDY_ROWS = 32;
+constexpr int GREEDY_COLS = 2 * GREEDY_ROWS + 1;
+
+__global__ void __launch_bounds__(32) k_greedy(const uint16_t *__restrict__ e, int H, int W,
+                                               int32_t *__restrict__ seam, int64_t *__restrict__ cost) {
+  __shared__ uint32_t win[GREEDY_ROWS][GREEDY_COLS + 1];
+  const int lane = threadIdx.x;
+  unsigned long long best = ~0ull;   // (energy << 32) | column, leftmost minimum
+  const uint16_t *last = e + (int64_t)(H - 1) * W;
+  for (int j = lane; j < W; j += 32) {
+    const unsigned long long k = ((unsigned long long)last[j] << 32) | (unsigned)j;
+    best = k < best ? k : best;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off);
+    best = o < best ? o : best;
+  }
+  int j = (int)(best & 0xFFFFFFFFu);
+  int64_t total = (int64_t)(best >> 32);
+  if (lane == 0) seam[H - 1] = j;
+  for (int top = H - 1; top > 0; top -= GREEDY_ROWS) {
+    const int rows = top < GREEDY_ROWS ? top : GREEDY_ROWS;   // rows top-1 .. top-rows
+    const int c0 = j - GREEDY_ROWS;
+    // stage 8 rows at a time with all their loads in flight (3 columns per lane per row)
+    for (int rb = 0; rb < rows; rb += 8) {
+      uint32_t v[8][3];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int r = rb + q;
+        const uint16_t *row = e + (int64_t)(top - 1 - (r < rows ? r : 0)) * W;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int c = lane + 32 * u, col = c0 + c;
+          v[q][u] = (r < rows && c < GREEDY_COLS && col >= 0 && col < W) ? (uint32_t)row[col] : 0x10000u;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int c = lane + 32 * u;
+          if (rb + q < rows && c < GREEDY_COLS) win[rb + q][c] = v[q][u];   // 0x10000: above any energy
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      int x = j - c0;
+      for (int r = 0; r < rows; ++r) {
+        int b = x - 1;
+        if (win[r][x] < win[r][b]) b = x;
+        if (win[r][x + 1] < win[r][b]) b = x + 1;
+        x = b;
+        total += win[r][x];
+        seam[top - 1 - r] = c0 + x;
+      }
+      j = c0 + x;
+    }
+    j = __shfl_sync(0xffffffffu, j, 0);
+    __syncwarp();
+  }
+  if (lane == 0 && cost) *cost = total;
+}
+
+cudaError_t launch_greedy(const uint16_t *e, int H, int W, int32_t *seam, int64_t *cost, cudaStream_t st) {
+  k_greedy<<<1, 32, 0, st>>>(e, H, W, seam, cost);
+  return cudaGetLastError();
+}
+
+}  // namespace sc

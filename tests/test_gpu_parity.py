@@ -63,6 +63,19 @@ def test_find_seam_parity(dev, H, W):
         np.testing.assert_array_equal(_np(seam), s_ref, err_msg=f"{H}x{W} {kind}")
 
 
+@pytest.mark.parametrize("H,W", SEAM_SHAPES)
+def test_greedy_seam_parity(dev, H, W):
+    """Algorithm 2 on the GPU equals the oracle's greedy seam and cost (ties, edges, 1-wide maps)."""
+    rng = np.random.default_rng(H * 7919 + W)
+    for kind, e in _energies(rng, H, W):
+        e = e.astype(np.uint16)
+        seam, cost = sc.greedy_seam(_to_dev(e, dev))
+        sc.check()
+        s_ref, c_ref = oracle.greedy_seam(e)
+        assert int(_np(cost)[0]) == c_ref, (H, W, kind)
+        np.testing.assert_array_equal(_np(seam), s_ref, err_msg=f"{H}x{W} {kind}")
+
+
 def test_find_seam_energy_range_rejected(dev):
     e = np.full((2000, 16), 60000, dtype=np.uint16)   # 2000 * 60000 >= 2^24
     sc.find_seam(_to_dev(e, dev))
