@@ -63,6 +63,8 @@ def _load():
             lib.orc_transpose.restype = None
             lib.orc_carve.argtypes = [P, i, i, i, i, i, P, P, P]
             lib.orc_carve.restype = ctypes.c_int
+            lib.orc_enlarge.argtypes = [P, i, i, i, i, P, P]
+            lib.orc_enlarge.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -165,3 +167,20 @@ def carve(img, target_w: int, target_h: int, with_log: bool = False):
     if with_log:
         return out, log[: nv * H + nh * target_w], costs[: nv + nh]
     return out
+
+
+def enlarge(img, target_w: int, with_cols: bool = False):
+    """Seam insertion (reading R9): widen to target_w = W + k, 1 <= k <= W - 1, by inserting a
+    rounded-up mean pixel right of every input pixel on one of the first k seams the carve would
+    remove. Returns the H x target_w x C image, or (image, cols) with ``with_cols`` (cols[t, i] =
+    the input column seam t deletes in row i)."""
+    a, H, W, C = _img(img)
+    k = int(target_w) - W
+    if not (1 <= k <= W - 1):
+        raise ValueError("target_w must satisfy W < target_w < 2 W")
+    out = np.empty((H, int(target_w), C), dtype=np.uint8)
+    cols = np.empty((k, H), dtype=np.int32)
+    rc = _load().orc_enlarge(_ptr(a), H, W, C, int(target_w), _ptr(out), _ptr(cols))
+    if rc != 0:
+        raise ValueError("orc_enlarge rejected its arguments")
+    return (out, cols) if with_cols else out

@@ -31,6 +31,12 @@
  *      of the in-range upper neighbours; its cost is the sum of e along its path.
  *   R8 horizontal seams: transpose, remove vertical seams, transpose back; all vertical seams
  *      are removed before the horizontal ones.
+ *   R9 seam insertion (enlargement, which the paper names as a use of seams without giving its
+ *      steps): to widen by k (1 <= k <= W-1), take the first k seams that the loop would remove
+ *      from the W-wide image, each mapped back to the input column it deletes; after every input
+ *      pixel on one of them insert one pixel whose channels are the rounded-up mean
+ *      (a + b + 1) / 2 of that pixel and its right neighbour (the pixel itself at the last
+ *      column, by the border clamp of R1).
  * Energies and costs are exact integers (int64 here), so no rounding question arises.
  */
 #include <stdint.h>
@@ -229,5 +235,52 @@ int orc_carve(const uint8_t *img, int H, int W, int C, int tw, int th, uint8_t *
   }
   free(buf);
   free(tmp);
+  return 0;
+}
+
+/* ---- seam insertion (reading R9) ----
+ * out receives H x tw x C with tw = W + k; cols (nullable) receives the k mapped input columns of
+ * every row, seam by seam (k*H entries). Returns 0, or -1 on bad arguments. */
+int orc_enlarge(const uint8_t *img, int H, int W, int C, int tw, uint8_t *out, int32_t *cols) {
+  const int k = tw - W;
+  if (H < 1 || W < 1 || C < 1 || k < 1 || k > W - 1) return -1;
+  size_t n = (size_t)H * W * C;
+  uint8_t *buf = (uint8_t *)malloc(n);
+  uint8_t *tmp = (uint8_t *)malloc(n);
+  int32_t *log = (int32_t *)malloc(sizeof(int32_t) * (size_t)k * H);
+  int *idx = (int *)malloc(sizeof(int) * W);
+  uint8_t *dup = (uint8_t *)malloc(W);
+  memcpy(buf, img, n);
+  carve_vertical(buf, tmp, H, W, C, k, log, NULL);   /* the k seams, each in its own image's columns */
+  for (int i = 0; i < H; ++i) {
+    /* input column of every current column, updated by deleting each seam's entry in turn */
+    for (int j = 0; j < W; ++j) idx[j] = j;
+    memset(dup, 0, W);
+    for (int t = 0; t < k; ++t) {
+      int c = log[(size_t)t * H + i];
+      int src = idx[c];
+      dup[src] = 1;
+      if (cols) cols[(size_t)t * H + i] = src;
+      memmove(idx + c, idx + c + 1, sizeof(int) * (size_t)(W - t - 1 - c));
+    }
+    const uint8_t *row = img + (size_t)i * W * C;
+    uint8_t *o = out + (size_t)i * tw * C;
+    int q = 0;
+    for (int j = 0; j < W; ++j) {
+      for (int ch = 0; ch < C; ++ch) o[(size_t)q * C + ch] = row[(size_t)j * C + ch];
+      ++q;
+      if (dup[j]) {
+        int jr = clampi(j + 1, 0, W - 1);
+        for (int ch = 0; ch < C; ++ch)
+          o[(size_t)q * C + ch] = (uint8_t)(((int)row[(size_t)j * C + ch] + (int)row[(size_t)jr * C + ch] + 1) / 2);
+        ++q;
+      }
+    }
+  }
+  free(buf);
+  free(tmp);
+  free(log);
+  free(idx);
+  free(dup);
   return 0;
 }

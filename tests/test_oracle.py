@@ -315,3 +315,54 @@ def test_config1_oracle_small():
         s1, c1 = oracle.dp_seam(crop)
         s2, c2, _ = oracle.brute_seam(crop)
         assert c1 == c2 and s1.tolist() == s2.tolist()
+
+
+# ---- seam insertion (reading R9) ----
+
+def _enlarge_cases():
+    rng = np.random.default_rng(917)
+    cases = []
+    for H, W, C in [(1, 2, 1), (1, 9, 3), (3, 2, 3), (4, 5, 1), (7, 12, 4), (16, 23, 3), (33, 40, 3), (50, 9, 1)]:
+        for kind in ("uniform", "ties"):
+            hi = 256 if kind == "uniform" else 3
+            img = rng.integers(0, hi, size=(H, W, C)).astype(np.uint8)
+            for k in sorted({1, max(1, W // 3), W - 1}):
+                cases.append((img, k))
+    return cases
+
+
+def test_enlarge_deleting_the_inserted_pixels_gives_the_input():
+    """Each row holds exactly k inserted pixels, right after k distinct input columns, with the
+    rounded-up mean of that pixel and its right neighbour; deleting them restores the row."""
+    for img, k in _enlarge_cases():
+        H, W, C = img.shape
+        out, cols = oracle.enlarge(img, W + k, with_cols=True)
+        assert out.shape == (H, W + k, C) and cols.shape == (k, H)
+        for i in range(H):
+            d = np.sort(cols[:, i])
+            assert len(set(d.tolist())) == k and d.min() >= 0 and d.max() < W
+            ins = d + np.arange(k) + 1                    # output positions of the inserted pixels
+            keep = np.setdiff1d(np.arange(W + k), ins)
+            np.testing.assert_array_equal(out[i, keep], img[i])
+            right = img[i, np.minimum(d + 1, W - 1)].astype(np.int32)
+            mean = (img[i, d].astype(np.int32) + right + 1) // 2
+            np.testing.assert_array_equal(out[i, ins], mean.astype(np.uint8))
+
+
+def test_enlarge_columns_are_the_carved_seams():
+    """The k mapped columns of a row are exactly the pixels the carve to W - k deletes from it."""
+    for img, k in _enlarge_cases():
+        H, W, C = img.shape
+        _, cols = oracle.enlarge(img, W + k, with_cols=True)
+        carved = oracle.carve(img, W - k, H)
+        for i in range(H):
+            keep = np.setdiff1d(np.arange(W), cols[:, i])
+            np.testing.assert_array_equal(img[i, keep], carved[i])
+
+
+def test_enlarge_constant_image_and_limits():
+    img = np.full((6, 10, 3), 77, dtype=np.uint8)
+    np.testing.assert_array_equal(oracle.enlarge(img, 19), np.full((6, 19, 3), 77, dtype=np.uint8))
+    for tw in (10, 20, 5):
+        with pytest.raises(ValueError):
+            oracle.enlarge(img, tw)
