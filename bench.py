@@ -360,6 +360,26 @@ def uhd_search_measurement(sc, torch, dev, steps, peak):
                     "its padded workspace (one extra kernel per map), the kernel figure excludes that"}
 
 
+def enlarge_measurement(sc, torch, dev, img):
+    """Seam insertion: the 1920x1080 image widened to 2400 (480 seams found by the carve, mapped
+    back to the input and inserted)."""
+    out = sc.enlarge(img, 2400)
+    torch.cuda.synchronize(dev)
+    ms = []
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sc.enlarge(img, 2400)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    sc.check()
+    t = statistics.median(ms) / 1000.0
+    return {"workload": "1920x1080 -> 2400x1080 (480 inserted seams)", "ms": 1e3 * t, "seams_per_s": 480 / t,
+            "out_shape": list(out.shape)}
+
+
 def paper_workload_measurement(sc, torch, dev, cpu: bool):
     """The paper's own workload ("Runtime For different sized images"): n x n images at n = 180,
     360, 480, 720, 1080 with s = 0.5, i.e. n/2 vertical seams. On the GPU: one DP seam search
@@ -591,6 +611,7 @@ def run_native(a):
     if rank == 0 and not a.no_4k:
         line["uhd_search_concurrent"] = uhd_search_measurement(sc, torch, dev, a.steps, peak)
     if rank == 0 and not a.no_paper:
+        line["enlarge_1920x1080"] = enlarge_measurement(sc, torch, dev, img)
         line["paper_nxn"] = paper_workload_measurement(sc, torch, dev, cpu=not a.no_cpu_baseline and ws == 1)
     if rank == 0 and serving_imgs is not None:
         line["serving"] = serving_measurement(sc, torch, dev, serving_imgs, a.serving_requests)

@@ -96,6 +96,18 @@ int sc_energy(const uint8_t *img, int H, int W, int C, uint16_t *energy_out, voi
  *         or energies that could overflow (checked on the device: SC_EINTERNAL via sc_check). */
 int sc_find_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_t *cost_out, void *stream);
 
+/* ---- seam insertion: widening by k = target_w - W seams (1 <= k <= W-1) ----
+ * The paper names enlargement by seams ("Seam Carving" background) without giving its steps; the
+ * reading implemented: take the first k seams that sc_carve(img, W - k, H) removes (Algorithm 3
+ * on each shrinking image), map each back to the input column it deletes in every row, and after
+ * every input pixel in one of those columns insert a pixel whose channels are the rounded-up mean
+ * (a + b + 1) / 2 of it and its right neighbour (the pixel itself at the last column).
+ * img: device H x W x C uint8 (C in {1,3,4}); out: device H x target_w x C; cols_out: device
+ * int32[k*H] or NULL, receiving the mapped input column of seam t in row i at t*H + i.
+ * Asynchronous on `stream`; uses the stream's workspace. Errors: SC_EINVAL for a null pointer, a
+ * bad shape or channel count, or target_w outside (W, 2W); device errors via sc_check. */
+int sc_enlarge(const uint8_t *img, int H, int W, int C, int target_w, uint8_t *out, int32_t *cols_out, void *stream);
+
 /* ---- Algorithm 2 (section "Greedy Seam Carving"): the greedy seam ----
  * Starts at the leftmost minimum of the bottom row and climbs, row by row, to the leftmost minimum
  * of the in-range upper neighbours (j-1, j, j+1); cost = the sum of the energies on the seam.

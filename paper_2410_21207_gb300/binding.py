@@ -64,6 +64,7 @@ def load(path: Optional[str] = None):
                 "sc_find_seam_static": ([P, I, I, P, P, P], I),
                 "sc_find_seam_multi": ([P, I, I, I, P, P, P], I),
                 "sc_greedy_seam": ([P, I, I, P, P, P], I),
+                "sc_enlarge": ([P, I, I, I, I, P, P, P], I),
                 "sc_find_seam_multi_capacity": ([I, I, P], I),
                 "sc_find_seam_multi_shape": ([I, I], I),
                 "sc_carve": ([P, I, I, I, I, I, P, P, P, P], I),
@@ -149,6 +150,21 @@ def find_seam(e):
     cost = torch.empty(1, dtype=torch.int64, device=e.device)
     _raise(load().sc_find_seam(_ptr(e), H, W, _ptr(seam), _ptr(cost), _stream(torch, e.device)))
     return seam, cost
+
+
+def enlarge(img, target_w: int, with_cols: bool = False):
+    """Seam insertion: widen a CUDA uint8 image (H x W x C or H x W) to target_w = W + k,
+    1 <= k <= W - 1. Returns the widened image, or (image, cols[k, H]) with ``with_cols``."""
+    torch = _torch()
+    _check_device_u8(img)
+    H, W, C = _img_shape(img)
+    k = int(target_w) - W
+    shape = (H, int(target_w)) if img.dim() == 2 else (H, int(target_w), C)
+    out = torch.empty(shape, dtype=torch.uint8, device=img.device)
+    cols = torch.empty((max(k, 1), H), dtype=torch.int32, device=img.device) if with_cols else None
+    _raise(load().sc_enlarge(_ptr(img), H, W, C, int(target_w), _ptr(out), _ptr(cols) if with_cols else None,
+                             _stream(torch, img.device)))
+    return (out, cols) if with_cols else out
 
 
 def greedy_seam(e):

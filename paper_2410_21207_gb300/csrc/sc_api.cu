@@ -106,6 +106,9 @@ struct Workspace {
   DevBuf<uint8_t> hin, hout;     // staging for the host-pointer entry point
   DevBuf<int> flags;             // [0] error word, [1] energy-range gate
   DevBuf<uint16_t> Emulti;       // padded maps of sc_find_seam_multi
+  DevBuf<int32_t> enl_log;       // sc_enlarge: the k seams, the carved copy, the widening bitmap
+  DevBuf<uint8_t> enl_tmp;
+  DevBuf<uint32_t> enl_bits;
   DevBuf<uint32_t> Mmulti;
   DevBuf<DpArgs> dargs;
   bool flags_zeroed = false;
@@ -113,6 +116,7 @@ struct Workspace {
     img.release(); img2.release(); Mrow.release();
     E.release(); seam.release(); lists.release(); hin.release(); hout.release(); flags.release();
     Emulti.release(); Mmulti.release(); dargs.release();
+    enl_log.release(); enl_tmp.release(); enl_bits.release();
     flags_zeroed = false;
   }
 };
@@ -439,6 +443,34 @@ int sc_find_seam_multi(const uint16_t *const *energies, int n, int H, int W, int
   }
   SC_CUDA(cudaMemcpyAsync(ws.dargs.p, h.data(), n * sizeof(DpArgs), cudaMemcpyHostToDevice, st));
   SC_CUDA(timed("dp_multi", st, [&] { return launch_dp_multi(ws.dargs.p, n, H, W, st); }));
+  return SC_OK;
+}
+
+int sc_enlarge(const uint8_t *img, int H, int W, int C, int target_w, uint8_t *out, int32_t *cols_out, void *stream) {
+  const int k = target_w - W;
+  if (!img || !out) return fail(SC_EINVAL, "null pointer");
+  if (k < 1 || k > W - 1) return fail(SC_EINVAL, "target_w %d outside (W, 2W) for W = %d", target_w, W);
+  int rc = check_carve_args(img, H, W, C, W - k, H, out);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace *wsp;
+  if ((rc = get_ws(stream, &wsp))) return rc;
+  Workspace &ws = *wsp;
+  const int nwords = (W + 31) / 32;
+  {
+    std::lock_guard<std::mutex> lk(ws.mu);
+    if ((rc = ensure_flags(ws, st))) return rc;
+    SC_CUDA(ws.enl_log.ensure((size_t)k * H));
+    SC_CUDA(ws.enl_tmp.ensure((size_t)H * (W - k) * C));
+    SC_CUDA(ws.enl_bits.ensure((size_t)H * nwords));
+  }
+  // the k seams the carve would remove, each in its own shrinking image's columns
+  if ((rc = carve_impl(img, H, W, C, W - k, H, ws.enl_tmp.p, ws.enl_log.p, nullptr, st))) return rc;
+  std::lock_guard<std::mutex> lk(ws.mu);
+  SC_CUDA(timed("enlarge_map", st, [&] {
+    return launch_enlarge_map(ws.enl_log.p, H, W, k, ws.enl_bits.p, cols_out, ws.flags.p, st);
+  }));
+  SC_CUDA(timed("insert", st, [&] { return launch_insert(img, H, W, C, ws.enl_bits.p, out, target_w, st); }));
   return SC_OK;
 }
 

@@ -76,6 +76,12 @@ cudaError_t dp_multi_capacity(int H, int W, int *n_out);
 int dp_multi_set_shape(int nw, int kt);
 // Algorithm 2's greedy seam of an unpadded H x W map (one warp)
 cudaError_t launch_greedy(const uint16_t *e, int H, int W, int32_t *seam, int64_t *cost, cudaStream_t st);
+// seam insertion (sc_enlarge.cu): seam log -> per-row bitmap of the input columns to widen at
+// (cols, nullable, receives them seam by seam); then the widened image
+cudaError_t launch_enlarge_map(const int32_t *log, int H, int W, int k, uint32_t *bits, int32_t *cols, int *err,
+                               cudaStream_t st);
+cudaError_t launch_insert(const uint8_t *img, int H, int W, int C, const uint32_t *bits, uint8_t *out, int tw,
+                          cudaStream_t st);
 // lazy image compaction (sc_rowops.cuh): refresh + list update per seam, bulk compaction
 cudaError_t launch_compact_lazy(uint32_t *img, int pitch, int H, int w, const int16_t *lists, int m, cudaStream_t st);
 // per seam: refreshed pair through the lazy map, list update and energy compaction (one warp per row)
