@@ -96,6 +96,13 @@ int sc_energy(const uint8_t *img, int H, int W, int C, uint16_t *energy_out, voi
  *         or energies that could overflow (checked on the device: SC_EINTERNAL via sc_check). */
 int sc_find_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_t *cost_out, void *stream);
 
+/* ---- failure-detection self-test (the paper has no counterpart) ----
+ * Enqueues one kernel whose single wait, the same bounded mbarrier wait the seam search uses,
+ * waits for an arrival that never comes; after limit_us (1 .. 1e6) it records a timeout in the
+ * stream's device error word and returns normally. The next sc_check(stream) then returns
+ * SC_ETIMEOUT, and the stream and context stay usable. Errors: SC_EINVAL for a limit out of range. */
+int sc_selftest_wait_timeout(int limit_us, void *stream);
+
 /* ---- seam insertion: widening by k = target_w - W seams (1 <= k <= W-1) ----
  * The paper names enlargement by seams ("Seam Carving" background) without giving its steps; the
  * reading implemented: take the first k seams that sc_carve(img, W - k, H) removes (Algorithm 3

@@ -65,6 +65,7 @@ def load(path: Optional[str] = None):
                 "sc_find_seam_multi": ([P, I, I, I, P, P, P], I),
                 "sc_greedy_seam": ([P, I, I, P, P, P], I),
                 "sc_enlarge": ([P, I, I, I, I, P, P, P], I),
+                "sc_selftest_wait_timeout": ([I, P], I),
                 "sc_find_seam_multi_capacity": ([I, I, P], I),
                 "sc_find_seam_multi_shape": ([I, I], I),
                 "sc_carve": ([P, I, I, I, I, I, P, P, P, P], I),
@@ -165,6 +166,12 @@ def enlarge(img, target_w: int, with_cols: bool = False):
     _raise(load().sc_enlarge(_ptr(img), H, W, C, int(target_w), _ptr(out), _ptr(cols) if with_cols else None,
                              _stream(torch, img.device)))
     return (out, cols) if with_cols else out
+
+
+def selftest_wait_timeout(limit_us: int = 1000) -> None:
+    """Enqueue the bounded-wait self-test on the current stream (sc_check then raises SC_ETIMEOUT)."""
+    torch = _torch()
+    _raise(load().sc_selftest_wait_timeout(int(limit_us), _stream(torch, torch.device("cuda", torch.cuda.current_device()))))
 
 
 def greedy_seam(e):

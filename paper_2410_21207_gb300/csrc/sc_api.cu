@@ -474,6 +474,18 @@ int sc_enlarge(const uint8_t *img, int H, int W, int C, int target_w, uint8_t *o
   return SC_OK;
 }
 
+int sc_selftest_wait_timeout(int limit_us, void *stream) {
+  if (limit_us < 1 || limit_us > 1000000) return fail(SC_EINVAL, "limit must be 1 us .. 1 s");
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace *wsp;
+  int rc = get_ws(stream, &wsp);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(wsp->mu);
+  if ((rc = ensure_flags(*wsp, st))) return rc;
+  SC_CUDA(launch_wait_selftest((uint64_t)limit_us * 1000u, wsp->flags.p, st));
+  return SC_OK;
+}
+
 int sc_greedy_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_t *cost_out, void *stream) {
   if (!energy || !seam_out) return fail(SC_EINVAL, "null pointer");
   if (H < 1 || W < 1 || H > SC_MAX_ROWS || W > SC_MAX_COLS) return fail(SC_EINVAL, "bad shape %d x %d", H, W);

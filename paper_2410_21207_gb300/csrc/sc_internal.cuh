@@ -82,6 +82,8 @@ cudaError_t launch_enlarge_map(const int32_t *log, int H, int W, int k, uint32_t
                                cudaStream_t st);
 cudaError_t launch_insert(const uint8_t *img, int H, int W, int C, const uint32_t *bits, uint8_t *out, int tw,
                           cudaStream_t st);
+// one bounded mbarrier wait that nothing completes (failure-detection self-test)
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int *err, cudaStream_t st);
 // lazy image compaction (sc_rowops.cuh): refresh + list update per seam, bulk compaction
 cudaError_t launch_compact_lazy(uint32_t *img, int pitch, int H, int w, const int16_t *lists, int m, cudaStream_t st);
 // per seam: refreshed pair through the lazy map, list update and energy compaction (one warp per row)

@@ -2,6 +2,7 @@
 // local energy refresh and row compaction (arXiv 2410.21207, sections "Energy Mapping" and
 // "Removal of Seams"; horizontal seams by transposition, section "Design Techniques").
 #include "sc_internal.cuh"
+#include "sc_ptx.cuh"
 #include "sc_rowops.cuh"
 
 namespace sc {
@@ -232,6 +233,27 @@ __global__ void __launch_bounds__(32) k_greedy(const uint16_t *__restrict__ e, i
 
 cudaError_t launch_greedy(const uint16_t *e, int H, int W, int32_t *seam, int64_t *cost, cudaStream_t st) {
   k_greedy<<<1, 32, 0, st>>>(e, H, W, seam, cost);
+  return cudaGetLastError();
+}
+
+}  // namespace sc
+
+namespace sc {
+
+// ---- self-test of the bounded waits: one thread waits on an mbarrier that nothing completes,
+// with a limit of limit_ns, exactly as the search's waits do; when the limit runs out it records
+// ERR_TIMEOUT and returns (no trap, no fault), so the host sees SC_ETIMEOUT and the context stays
+// usable. ----
+__global__ void k_wait_selftest(uint64_t limit_ns, int *err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);   // one arrival expected; none comes
+  fence_mbar_init();
+  if (!mbar_wait_bounded(&bar, 0u, limit_ns)) atomicOr(err, ERR_TIMEOUT);
+}
+
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int *err, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(limit_ns, err);
   return cudaGetLastError();
 }
 

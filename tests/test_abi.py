@@ -55,6 +55,7 @@ def test_argument_errors_are_synchronous():
     assert lib.sc_enlarge(fake, 10, 10, 3, 20, fake, P(0), P(0)) == binding.SC_EINVAL   # k = W
     assert lib.sc_enlarge(P(0), 10, 10, 3, 15, fake, P(0), P(0)) == binding.SC_EINVAL
     assert lib.sc_greedy_seam(P(0), 10, 10, fake, P(0), P(0)) == binding.SC_EINVAL
+    assert lib.sc_selftest_wait_timeout(0, P(0)) == binding.SC_EINVAL
     assert lib.sc_find_seam_multi_shape(5, 8) == binding.SC_EINVAL
     assert lib.sc_find_seam_multi_shape(0, 0) == binding.SC_OK
     maps = (P * 2)(fake, P(0))
