@@ -65,6 +65,12 @@ def _load():
             lib.orc_carve.restype = ctypes.c_int
             lib.orc_enlarge.argtypes = [P, i, i, i, i, P, P]
             lib.orc_enlarge.restype = ctypes.c_int
+            lib.orc_forward_costs.argtypes = [P, i, i, i, P, P, P]
+            lib.orc_forward_costs.restype = None
+            lib.orc_dp_seam_forward.argtypes = [P, P, P, i, i, P]
+            lib.orc_dp_seam_forward.restype = ctypes.c_int64
+            lib.orc_carve_forward.argtypes = [P, i, i, i, i, i, P, P, P]
+            lib.orc_carve_forward.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -184,3 +190,42 @@ def enlarge(img, target_w: int, with_cols: bool = False):
     if rc != 0:
         raise ValueError("orc_enlarge rejected its arguments")
     return (out, cols) if with_cols else out
+
+
+def forward_costs(img) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Forward energy (reading R10): the CU, DL, DR planes (uint16 H x W) of an image."""
+    a, H, W, C = _img(img)
+    cu = np.empty((H, W), dtype=np.uint16)
+    dl = np.empty((H, W), dtype=np.uint16)
+    dr = np.empty((H, W), dtype=np.uint16)
+    _load().orc_forward_costs(_ptr(a), H, W, C, _ptr(cu), _ptr(dl), _ptr(dr))
+    return cu, dl, dr
+
+
+def dp_seam_forward(cu, dl, dr) -> tuple[np.ndarray, int]:
+    """Algorithm 3 with forward costs: (seam[H] int32, cost)."""
+    cu = np.ascontiguousarray(cu, dtype=np.uint16)
+    dl = np.ascontiguousarray(dl, dtype=np.uint16)
+    dr = np.ascontiguousarray(dr, dtype=np.uint16)
+    H, W = cu.shape
+    s = np.empty(H, dtype=np.int32)
+    cost = _load().orc_dp_seam_forward(_ptr(cu), _ptr(dl), _ptr(dr), H, W, _ptr(s))
+    return s, int(cost)
+
+
+def carve_forward(img, target_w: int, target_h: int, with_log: bool = False):
+    """The full loop with forward energy (as carve, the forward costs recomputed per seam)."""
+    a, H, W, C = _img(img)
+    if not (1 <= target_w <= W and 1 <= target_h <= H):
+        raise ValueError("targets must satisfy 1 <= target <= size")
+    out = np.empty((target_h, target_w, C), dtype=np.uint8)
+    nv, nh = W - target_w, H - target_h
+    log = np.empty(max(1, nv * H + nh * target_w), dtype=np.int32)
+    costs = np.empty(max(1, nv + nh), dtype=np.int64)
+    rc = _load().orc_carve_forward(_ptr(a), H, W, C, int(target_w), int(target_h), _ptr(out), _ptr(log),
+                                   _ptr(costs))
+    if rc != 0:
+        raise ValueError("orc_carve_forward rejected its arguments")
+    if with_log:
+        return out, log[: nv * H + nh * target_w], costs[: nv + nh]
+    return out

@@ -37,6 +37,12 @@
  *      pixel on one of them insert one pixel whose channels are the rounded-up mean
  *      (a + b + 1) / 2 of that pixel and its right neighbour (the pixel itself at the last
  *      column, by the border clamp of R1).
+ *   R10 forward energy (the paper cites it as an alternative criterion without a formula): the
+ *      cost of a seam is the sum, over the pixel pairs that become adjacent when it is removed, of
+ *      their L1 colour difference. Per pixel (i, j) with the seam arriving from (i-1, j') this is
+ *      CU = |I(i,j+1) - I(i,j-1)| (0 when j is the first or last column: no new horizontal pair),
+ *      plus DL = |I(i-1,j) - I(i,j-1)| when j' = j-1, or DR = |I(i-1,j) - I(i,j+1)| when j' = j+1;
+ *      row 0 costs CU only. The DP is Algorithm 3 with these per-direction costs, with R3-R5.
  * Energies and costs are exact integers (int64 here), so no rounding question arises.
  */
 #include <stdint.h>
@@ -282,5 +288,106 @@ int orc_enlarge(const uint8_t *img, int H, int W, int C, int tw, uint8_t *out, i
   free(log);
   free(idx);
   free(dup);
+  return 0;
+}
+
+/* ---- forward energy (reading R10) ----
+ * Three planes of H x W: CU, DL, DR (zero where the pair does not exist). */
+void orc_forward_costs(const uint8_t *img, int H, int W, int C, uint16_t *cu, uint16_t *dl, uint16_t *dr) {
+  for (int i = 0; i < H; ++i) {
+    for (int j = 0; j < W; ++j) {
+      int u = 0, l = 0, r = 0;
+      for (int c = 0; c < C; ++c) {
+        if (j >= 1 && j + 1 < W)
+          u += absi((int)img[((size_t)i * W + j + 1) * C + c] - (int)img[((size_t)i * W + j - 1) * C + c]);
+        if (i >= 1 && j >= 1)
+          l += absi((int)img[((size_t)(i - 1) * W + j) * C + c] - (int)img[((size_t)i * W + j - 1) * C + c]);
+        if (i >= 1 && j + 1 < W)
+          r += absi((int)img[((size_t)(i - 1) * W + j) * C + c] - (int)img[((size_t)i * W + j + 1) * C + c]);
+      }
+      cu[(size_t)i * W + j] = (uint16_t)u;
+      dl[(size_t)i * W + j] = (uint16_t)l;
+      dr[(size_t)i * W + j] = (uint16_t)r;
+    }
+  }
+}
+
+/* Algorithm 3 with the forward costs: M(0,j) = CU(0,j); M(i,j) = CU(i,j) + min over in-range
+ * j' in (j-1, j, j+1) of M(i-1,j') + (DL(i,j) if j' = j-1, 0 if j' = j, DR(i,j) if j' = j+1),
+ * the leftmost candidate winning ties; backtrack and last-row argmin as R4, R5. */
+int64_t orc_dp_seam_forward(const uint16_t *cu, const uint16_t *dl, const uint16_t *dr, int H, int W, int32_t *seam) {
+  int64_t *M = (int64_t *)malloc(sizeof(int64_t) * (size_t)H * W);
+  int32_t *B = (int32_t *)malloc(sizeof(int32_t) * (size_t)H * W);
+  for (int j = 0; j < W; ++j) { M[j] = cu[j]; B[j] = -1; }
+  for (int i = 1; i < H; ++i) {
+    for (int j = 0; j < W; ++j) {
+      int best = -1;
+      int64_t bestv = 0;
+      for (int jp = j - 1; jp <= j + 1; ++jp) {
+        if (jp < 0 || jp >= W) continue;
+        int64_t v = M[(size_t)(i - 1) * W + jp];
+        if (jp == j - 1) v += dl[(size_t)i * W + j];
+        if (jp == j + 1) v += dr[(size_t)i * W + j];
+        if (best < 0 || v < bestv) { best = jp; bestv = v; }
+      }
+      B[(size_t)i * W + j] = best;
+      M[(size_t)i * W + j] = (int64_t)cu[(size_t)i * W + j] + bestv;
+    }
+  }
+  int jstar = 0;
+  for (int j = 1; j < W; ++j)
+    if (M[(size_t)(H - 1) * W + j] < M[(size_t)(H - 1) * W + jstar]) jstar = j;
+  int64_t cost = M[(size_t)(H - 1) * W + jstar];
+  seam[H - 1] = jstar;
+  for (int i = H - 1; i >= 1; --i) seam[i - 1] = B[(size_t)i * W + seam[i]];
+  free(M);
+  free(B);
+  return cost;
+}
+
+/* The full loop with forward energy: (W - tw) vertical seams, then (H - th) horizontal seams on the
+ * transposed image, the forward costs recomputed from the current image before every seam. */
+static void carve_vertical_forward(uint8_t *buf, uint8_t *tmp, int H, int W, int C, int count, int32_t *seam_log,
+                                   int64_t *cost_log) {
+  size_t n = (size_t)H * W;
+  uint16_t *cu = (uint16_t *)malloc(sizeof(uint16_t) * n);
+  uint16_t *dl = (uint16_t *)malloc(sizeof(uint16_t) * n);
+  uint16_t *dr = (uint16_t *)malloc(sizeof(uint16_t) * n);
+  int32_t *seam = (int32_t *)malloc(sizeof(int32_t) * H);
+  for (int t = 0; t < count; ++t) {
+    int w = W - t;
+    orc_forward_costs(buf, H, w, C, cu, dl, dr);
+    int64_t cost = orc_dp_seam_forward(cu, dl, dr, H, w, seam);
+    if (seam_log) memcpy(seam_log + (size_t)t * H, seam, sizeof(int32_t) * H);
+    if (cost_log) cost_log[t] = cost;
+    orc_remove_seam(buf, H, w, C, seam, tmp);
+    memcpy(buf, tmp, (size_t)H * (w - 1) * C);
+  }
+  free(cu);
+  free(dl);
+  free(dr);
+  free(seam);
+}
+
+int orc_carve_forward(const uint8_t *img, int H, int W, int C, int tw, int th, uint8_t *out, int32_t *seam_log,
+                      int64_t *cost_log) {
+  if (H < 1 || W < 1 || C < 1 || tw < 1 || th < 1 || tw > W || th > H) return -1;
+  size_t n = (size_t)H * W * C;
+  uint8_t *buf = (uint8_t *)malloc(n);
+  uint8_t *tmp = (uint8_t *)malloc(n);
+  memcpy(buf, img, n);
+  int nv = W - tw, nh = H - th;
+  carve_vertical_forward(buf, tmp, H, W, C, nv, seam_log, cost_log);
+  if (nh > 0) {
+    orc_transpose(buf, H, tw, C, tmp);
+    memcpy(buf, tmp, (size_t)H * tw * C);
+    carve_vertical_forward(buf, tmp, tw, H, C, nh, seam_log ? seam_log + (size_t)nv * H : NULL,
+                           cost_log ? cost_log + nv : NULL);
+    orc_transpose(buf, tw, th, C, out);
+  } else {
+    memcpy(out, buf, (size_t)H * tw * C);
+  }
+  free(buf);
+  free(tmp);
   return 0;
 }

@@ -366,3 +366,101 @@ def test_enlarge_constant_image_and_limits():
     for tw in (10, 20, 5):
         with pytest.raises(ValueError):
             oracle.enlarge(img, tw)
+
+
+# ---- forward energy (reading R10) ----
+
+def _new_pair_cost(img, seam):
+    """Sum of the L1 colour differences of the pixel pairs that are adjacent in the image with
+    `seam` removed but were not adjacent before: computed from the two images alone."""
+    H, W, C = img.shape
+    src = [[j for j in range(W) if j != seam[i]] for i in range(H)]   # input column of each output pixel
+    tot = 0
+    img = img.astype(np.int64)
+
+    def diff(a, b):
+        return int(np.abs(img[a] - img[b]).sum())
+
+    for i in range(H):
+        for jj in range(W - 1):
+            if jj + 1 < W - 1:
+                a, b = (i, src[i][jj]), (i, src[i][jj + 1])
+                if abs(a[1] - b[1]) != 1:
+                    tot += diff(a, b)
+            if i + 1 < H:
+                a, b = (i, src[i][jj]), (i + 1, src[i + 1][jj])
+                if a[1] != b[1]:
+                    tot += diff(a, b)
+    return tot
+
+
+def _all_seams(H, W):
+    """Every 8-connected seam, bottom column ascending, each step up col-1, col, col+1."""
+    def up(i, col, path):
+        if i < 0:
+            yield list(reversed(path))
+            return
+        for c in (col - 1, col, col + 1):
+            if 0 <= c < W:
+                yield from up(i - 1, c, path + [c])
+    for col in range(W):
+        yield from up(H - 2, col, [col])
+
+
+def _path_cost(planes, seam):
+    cu, dl, dr = planes
+    c = int(cu[0, seam[0]])
+    for i in range(1, len(seam)):
+        j, jp = seam[i], seam[i - 1]
+        c += int(cu[i, j]) + (int(dl[i, j]) if jp == j - 1 else 0) + (int(dr[i, j]) if jp == j + 1 else 0)
+    return c
+
+
+def test_forward_costs_are_the_new_adjacencies():
+    """Along any seam, the forward costs add up to the colour differences of the pairs its removal
+    makes adjacent (borders included): the planes are pinned to what forward energy means."""
+    rng = np.random.default_rng(2008)
+    for H, W, C in [(1, 2, 1), (1, 5, 3), (2, 2, 3), (3, 4, 1), (4, 5, 3), (5, 6, 4), (6, 3, 3)]:
+        for _ in range(4):
+            img = rng.integers(0, 256, size=(H, W, C)).astype(np.uint8)
+            planes = oracle.forward_costs(img)
+            seams = list(_all_seams(H, W))
+            for s in seams[:: max(1, len(seams) // 40)]:
+                assert _path_cost(planes, s) == _new_pair_cost(img, s), (H, W, C, s)
+
+
+def test_forward_dp_equals_brute_force():
+    """The forward DP seam is the first strictly cheapest seam of the exhaustive enumeration (the
+    lexicographically smallest optimal seam read bottom to top), cost included."""
+    rng = np.random.default_rng(2009)
+    for H, W in [(1, 1), (1, 6), (2, 3), (3, 3), (4, 5), (5, 6), (6, 4), (3, 8)]:
+        for kind in ("uniform", "ties"):
+            for _ in range(6):
+                hi = 256 if kind == "uniform" else 2
+                img = rng.integers(0, hi, size=(H, W, 3)).astype(np.uint8)
+                planes = oracle.forward_costs(img)
+                best, best_s = None, None
+                for s in _all_seams(H, W):
+                    c = _path_cost(planes, s)
+                    if best is None or c < best:
+                        best, best_s = c, s
+                seam, cost = oracle.dp_seam_forward(*planes)
+                assert cost == best, (H, W, kind)
+                np.testing.assert_array_equal(seam, best_s)
+
+
+def test_forward_carve_invariants():
+    img = np.full((7, 9, 3), 40, dtype=np.uint8)
+    np.testing.assert_array_equal(oracle.carve_forward(img, 5, 4), np.full((4, 5, 3), 40, dtype=np.uint8))
+    rng = np.random.default_rng(2010)
+    img = rng.integers(0, 256, size=(12, 15, 3)).astype(np.uint8)
+    out, log, costs = oracle.carve_forward(img, 10, 12, with_log=True)
+    cur = img
+    for t in range(5):
+        s = log[t * 12:(t + 1) * 12]
+        assert costs[t] == _new_pair_cost(cur, s)   # each removal's cost is what it makes adjacent
+        cur = oracle.remove_seam(cur, s)
+    np.testing.assert_array_equal(out, cur)
+    # horizontal seams are the vertical seams of the transposed image
+    t_out = oracle.carve_forward(img.transpose(1, 0, 2).copy(), 10, 15)
+    np.testing.assert_array_equal(oracle.carve_forward(img, 15, 10), t_out.transpose(1, 0, 2))
