@@ -360,6 +360,24 @@ def uhd_search_measurement(sc, torch, dev, steps, peak):
                     "its padded workspace (one extra kernel per map), the kernel figure excludes that"}
 
 
+def forward_measurement(sc, torch, dev, img, tw, th, seams):
+    """The headline carve with forward energy instead of e1 (three cost planes per pixel)."""
+    sc.carve_forward(img, tw, th)
+    torch.cuda.synchronize(dev)
+    ms = []
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sc.carve_forward(img, tw, th)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    sc.check()
+    t = statistics.median(ms) / 1000.0
+    return {"workload": "1920x1080 -> 1440x1080, forward energy", "ms_per_carve": 1e3 * t, "seams_per_s": seams / t}
+
+
 def enlarge_measurement(sc, torch, dev, img):
     """Seam insertion: the 1920x1080 image widened to 2400 (480 seams found by the carve, mapped
     back to the input and inserted)."""
@@ -612,6 +630,7 @@ def run_native(a):
         line["uhd_search_concurrent"] = uhd_search_measurement(sc, torch, dev, a.steps, peak)
     if rank == 0 and not a.no_paper:
         line["enlarge_1920x1080"] = enlarge_measurement(sc, torch, dev, img)
+        line["forward_energy_1920x1080"] = forward_measurement(sc, torch, dev, img, tw, th, seams)
         line["paper_nxn"] = paper_workload_measurement(sc, torch, dev, cpu=not a.no_cpu_baseline and ws == 1)
     if rank == 0 and serving_imgs is not None:
         line["serving"] = serving_measurement(sc, torch, dev, serving_imgs, a.serving_requests)

@@ -96,6 +96,26 @@ int sc_energy(const uint8_t *img, int H, int W, int C, uint16_t *energy_out, voi
  *         or energies that could overflow (checked on the device: SC_EINTERNAL via sc_check). */
 int sc_find_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_t *cost_out, void *stream);
 
+/* ---- forward energy (the paper cites it as an alternative to e1 without a formula) ----
+ * Reading implemented: a seam costs the sum, over the pixel pairs its removal makes adjacent, of
+ * their L1 colour difference. Per pixel (i, j): CU = |I(i,j+1) - I(i,j-1)| (0 at the first and
+ * last column), DL = |I(i-1,j) - I(i,j-1)| (0 in row 0 / column 0), DR = |I(i-1,j) - I(i,j+1)|
+ * (0 in row 0 / the last column), channels summed. Algorithm 3 with direction-dependent costs:
+ * M(0,j) = CU(0,j); M(i,j) = CU(i,j) + min(M(i-1,j-1) + DL(i,j), M(i-1,j), M(i-1,j+1) + DR(i,j)),
+ * leftmost ties, leftmost last-row minimum.
+ * sc_forward_costs: the three uint16 H x W planes of a device image (C in {1,3,4}).
+ * sc_find_seam_forward: the seam of caller planes (device uint16 H x W each; DL/DR entries with no
+ *   predecessor are ignored); W <= 4096; range check as sc_find_seam on CU + max(DL, DR).
+ * sc_carve_forward: sc_carve with forward energy (same arguments, seam and cost logs); every
+ *   searched width (W, and H when target_h < H) must be <= 4096.
+ * All asynchronous on `stream`. Errors: SC_EINVAL for null pointers or shapes out of range; device
+ * errors via sc_check. */
+int sc_forward_costs(const uint8_t *img, int H, int W, int C, uint16_t *cu, uint16_t *dl, uint16_t *dr, void *stream);
+int sc_find_seam_forward(const uint16_t *cu, const uint16_t *dl, const uint16_t *dr, int H, int W, int32_t *seam_out,
+                         int64_t *cost_out, void *stream);
+int sc_carve_forward(const uint8_t *img, int H, int W, int C, int target_w, int target_h, uint8_t *out,
+                     int32_t *seam_log, int64_t *cost_log, void *stream);
+
 /* ---- failure-detection self-test (the paper has no counterpart) ----
  * Enqueues one kernel whose single wait, the same bounded mbarrier wait the seam search uses,
  * waits for an arrival that never comes; after limit_us (1 .. 1e6) it records a timeout in the

@@ -66,6 +66,9 @@ def load(path: Optional[str] = None):
                 "sc_greedy_seam": ([P, I, I, P, P, P], I),
                 "sc_enlarge": ([P, I, I, I, I, P, P, P], I),
                 "sc_selftest_wait_timeout": ([I, P], I),
+                "sc_forward_costs": ([P, I, I, I, P, P, P, P], I),
+                "sc_find_seam_forward": ([P, P, P, I, I, P, P, P], I),
+                "sc_carve_forward": ([P, I, I, I, I, I, P, P, P, P], I),
                 "sc_find_seam_multi_capacity": ([I, I, P], I),
                 "sc_find_seam_multi_shape": ([I, I], I),
                 "sc_carve": ([P, I, I, I, I, I, P, P, P, P], I),
@@ -172,6 +175,50 @@ def selftest_wait_timeout(limit_us: int = 1000) -> None:
     """Enqueue the bounded-wait self-test on the current stream (sc_check then raises SC_ETIMEOUT)."""
     torch = _torch()
     _raise(load().sc_selftest_wait_timeout(int(limit_us), _stream(torch, torch.device("cuda", torch.cuda.current_device()))))
+
+
+def forward_costs(img):
+    """Forward-energy planes (CU, DL, DR) of a CUDA uint8 image: three H x W uint16 CUDA tensors."""
+    torch = _torch()
+    _check_device_u8(img)
+    H, W, C = _img_shape(img)
+    planes = [torch.empty((H, W), dtype=torch.uint16, device=img.device) for _ in range(3)]
+    _raise(load().sc_forward_costs(_ptr(img), H, W, C, *[_ptr(t) for t in planes], _stream(torch, img.device)))
+    return tuple(planes)
+
+
+def find_seam_forward(cu, dl, dr):
+    """Algorithm 3 with forward costs on three H x W uint16 CUDA planes -> (int32[H] seam, int64[1] cost)."""
+    torch = _torch()
+    for t in (cu, dl, dr):
+        if t.device.type != "cuda" or t.dtype != torch.uint16 or t.dim() != 2 or not t.is_contiguous() or t.shape != cu.shape:
+            raise ValueError("planes must be contiguous H x W uint16 CUDA tensors of one shape")
+    H, W = cu.shape
+    seam = torch.empty(H, dtype=torch.int32, device=cu.device)
+    cost = torch.empty(1, dtype=torch.int64, device=cu.device)
+    _raise(load().sc_find_seam_forward(_ptr(cu), _ptr(dl), _ptr(dr), H, W, _ptr(seam), _ptr(cost),
+                                       _stream(torch, cu.device)))
+    return seam, cost
+
+
+def carve_forward(img, target_w: int, target_h: int, with_log: bool = False):
+    """sc_carve with forward energy; returns the carved image (and the seam and cost logs)."""
+    torch = _torch()
+    _check_device_u8(img)
+    H, W, C = _img_shape(img)
+    shape = (target_h, target_w) if img.dim() == 2 else (target_h, target_w, C)
+    out = torch.empty(shape, dtype=torch.uint8, device=img.device)
+    log = cost = None
+    if with_log:
+        n = (W - target_w) * H + (H - target_h) * target_w
+        log = torch.empty(max(n, 1), dtype=torch.int32, device=img.device)
+        cost = torch.empty(max(W - target_w + H - target_h, 1), dtype=torch.int64, device=img.device)
+    _raise(load().sc_carve_forward(_ptr(img), H, W, C, int(target_w), int(target_h), _ptr(out), _ptr(log), _ptr(cost),
+                                   _stream(torch, img.device)))
+    if with_log:
+        nv, nh = W - target_w, H - target_h
+        return out, log[: nv * H + nh * target_w], cost[: nv + nh]
+    return out
 
 
 def greedy_seam(e):

@@ -188,8 +188,9 @@ int workspace_reserve(cudaStream_t st, int H, int W) {
 }
 
 static int launch_search(Workspace &ws, uint16_t *Ebase, int pe, int H, int W, int32_t *seam, int32_t *seam_log,
-                         int64_t *cost, const int *gate, cudaStream_t st) {
+                         int64_t *cost, const int *gate, cudaStream_t st, int64_t pstride = 0) {
   DpArgs a;
+  a.pstride = pstride;
   a.E = Ebase + E_PADL;
   a.pitch_e = pe;
   a.H = H;
@@ -209,7 +210,7 @@ static int launch_search(Workspace &ws, uint16_t *Ebase, int pe, int H, int W, i
 // lists, adds the removal to the row's list and compacts the energy row. The image words are
 // compacted every RPEND seams and at the end of the pass.
 static int carve_pass_plain(Workspace &ws, uint32_t *img, int pitch, int H, int W, int count, int pe,
-                            int32_t *seam_log, int64_t *cost_log, cudaStream_t st) {
+                            int32_t *seam_log, int64_t *cost_log, cudaStream_t st, int64_t pstride = 0) {
   int16_t *lb[2] = {ws.lists.p, ws.lists.p + (size_t)H * RPEND};
   int cur = 0, m = 0;
   for (int t = 0; t < count; ++t) {
@@ -225,9 +226,13 @@ static int carve_pass_plain(Workspace &ws, uint32_t *img, int pitch, int H, int 
     a.cost = cost_log ? cost_log + t : nullptr;
     a.err = ws.flags.p;
     a.gate = nullptr;
+    a.pstride = pstride;
     SC_CUDA(timed("dp", st, [&] { return launch_dp(a, st); }));
     SC_CUDA(timed("refresh", st, [&] {
-      return launch_refresh(img, pitch, ws.E.p + E_PADL, pe, H, w, ws.seam.p, lb[cur], lb[cur ^ 1], m, ws.flags.p, st);
+      return pstride ? launch_refresh_fwd(img, pitch, ws.E.p + E_PADL, pe, pstride, H, w, ws.seam.p, lb[cur],
+                                          lb[cur ^ 1], m, ws.flags.p, st)
+                     : launch_refresh(img, pitch, ws.E.p + E_PADL, pe, H, w, ws.seam.p, lb[cur], lb[cur ^ 1], m,
+                                      ws.flags.p, st);
     }));
     cur ^= 1;
     if (++m == RPEND) {
@@ -252,7 +257,7 @@ int check_carve_args(const void *img, int H, int W, int C, int tw, int th, const
 }
 
 int carve_impl(const uint8_t *img, int H, int W, int C, int tw, int th, uint8_t *out, int32_t *seam_log,
-               int64_t *cost_log, cudaStream_t st) {
+               int64_t *cost_log, cudaStream_t st, bool forward) {
   Workspace *wsp;
   int rc = get_ws((void *)st, &wsp);
   if (rc) return rc;
@@ -263,16 +268,23 @@ int carve_impl(const uint8_t *img, int H, int W, int C, int tw, int th, uint8_t 
   const int R = H > W ? H : W;
   const int pitch = round_up(R, 4);
   const int pe = pitch_e_for(R);
+  // forward energy keeps three cost planes, R rows apart
+  const int64_t pstride = forward ? (int64_t)R * pe : 0;
+  if (forward) SC_CUDA(ws.E.ensure((size_t)3 * R * pe));
+  auto energy = [&](const uint32_t *words, int rows, int cols) {
+    return forward ? launch_forward(words, pitch, rows, cols, ws.E.p + E_PADL, pe, pstride, st)
+                   : launch_energy(words, pitch, rows, cols, ws.E.p + E_PADL, pe, st);
+  };
   SC_CUDA(timed("pack", st, [&] { return launch_pack(img, H, W, C, ws.img.p, pitch, st); }));
-  SC_CUDA(timed("energy", st, [&] { return launch_energy(ws.img.p, pitch, H, W, ws.E.p + E_PADL, pe, st); }));
+  SC_CUDA(timed("energy", st, [&] { return energy(ws.img.p, H, W); }));
   const int nv = W - tw, nh = H - th;
-  rc = carve_pass_plain(ws, ws.img.p, pitch, H, W, nv, pe, seam_log, cost_log, st);
+  rc = carve_pass_plain(ws, ws.img.p, pitch, H, W, nv, pe, seam_log, cost_log, st, pstride);
   if (rc) return rc;
   if (nh > 0) {
     SC_CUDA(timed("transpose", st, [&] { return launch_transpose(ws.img.p, pitch, H, tw, ws.img2.p, pitch, st); }));  // tw x H
-    SC_CUDA(timed("energy", st, [&] { return launch_energy(ws.img2.p, pitch, tw, H, ws.E.p + E_PADL, pe, st); }));
+    SC_CUDA(timed("energy", st, [&] { return energy(ws.img2.p, tw, H); }));
     rc = carve_pass_plain(ws, ws.img2.p, pitch, tw, H, nh, pe, seam_log ? seam_log + (size_t)nv * H : nullptr,
-                          cost_log ? cost_log + nv : nullptr, st);
+                          cost_log ? cost_log + nv : nullptr, st, pstride);
     if (rc) return rc;
     SC_CUDA(timed("transpose", st, [&] { return launch_transpose(ws.img2.p, pitch, tw, th, ws.img.p, pitch, st); }));  // th x tw
   }
@@ -444,6 +456,62 @@ int sc_find_seam_multi(const uint16_t *const *energies, int n, int H, int W, int
   SC_CUDA(cudaMemcpyAsync(ws.dargs.p, h.data(), n * sizeof(DpArgs), cudaMemcpyHostToDevice, st));
   SC_CUDA(timed("dp_multi", st, [&] { return launch_dp_multi(ws.dargs.p, n, H, W, st); }));
   return SC_OK;
+}
+
+int sc_carve_forward(const uint8_t *img, int H, int W, int C, int target_w, int target_h, uint8_t *out,
+                     int32_t *seam_log, int64_t *cost_log, void *stream) {
+  int rc = check_carve_args(img, H, W, C, target_w, target_h, out);
+  if (rc) return rc;
+  const int need = target_h < H ? (W > H ? W : H) : W;
+  if (need > dp_forward_max_width())
+    return fail(SC_EINVAL, "forward energy searches at most %d columns (this carve needs %d)", dp_forward_max_width(),
+                need);
+  return carve_impl(img, H, W, C, target_w, target_h, out, seam_log, cost_log, (cudaStream_t)stream, true);
+}
+
+int sc_forward_costs(const uint8_t *img, int H, int W, int C, uint16_t *cu, uint16_t *dl, uint16_t *dr,
+                     void *stream) {
+  if (!img || !cu || !dl || !dr) return fail(SC_EINVAL, "null pointer");
+  if (H < 1 || W < 1 || H > SC_MAX_ROWS || W > SC_MAX_COLS || !valid_c(C))
+    return fail(SC_EINVAL, "bad shape %d x %d x %d", H, W, C);
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace *wsp;
+  int rc = get_ws(stream, &wsp);
+  if (rc) return rc;
+  Workspace &ws = *wsp;
+  std::lock_guard<std::mutex> lk(ws.mu);
+  const int pitch = round_up(W, 4);
+  const int pe = pitch_e_for(W);
+  const int64_t pstride = (int64_t)H * pe;
+  SC_CUDA(ws.img.ensure((size_t)H * pitch));
+  SC_CUDA(ws.E.ensure((size_t)3 * H * pe));
+  SC_CUDA(launch_pack(img, H, W, C, ws.img.p, pitch, st));
+  SC_CUDA(launch_forward(ws.img.p, pitch, H, W, ws.E.p + E_PADL, pe, pstride, st));
+  SC_CUDA(launch_unpad_energy(ws.E.p + E_PADL, pe, H, W, cu, st));
+  SC_CUDA(launch_unpad_energy(ws.E.p + E_PADL + pstride, pe, H, W, dl, st));
+  SC_CUDA(launch_unpad_energy(ws.E.p + E_PADL + 2 * pstride, pe, H, W, dr, st));
+  return SC_OK;
+}
+
+int sc_find_seam_forward(const uint16_t *cu, const uint16_t *dl, const uint16_t *dr, int H, int W, int32_t *seam_out,
+                         int64_t *cost_out, void *stream) {
+  if (!cu || !dl || !dr || !seam_out) return fail(SC_EINVAL, "null pointer");
+  if (H < 1 || W < 1 || H > SC_MAX_ROWS || W > dp_forward_max_width())
+    return fail(SC_EINVAL, "bad shape %d x %d (forward energy takes at most %d columns)", H, W, dp_forward_max_width());
+  cudaStream_t st = (cudaStream_t)stream;
+  Workspace *wsp;
+  int rc = get_ws(stream, &wsp);
+  if (rc) return rc;
+  Workspace &ws = *wsp;
+  std::lock_guard<std::mutex> lk(ws.mu);
+  if ((rc = ensure_flags(ws, st))) return rc;
+  const int pe = pitch_e_for(W);
+  const int64_t pstride = (int64_t)H * pe;
+  SC_CUDA(ws.E.ensure((size_t)3 * H * pe));
+  SC_CUDA(ws.Mrow.ensure((size_t)((H + KS - 1) / KS + 1) * pe));
+  SC_CUDA(cudaMemsetAsync(ws.flags.p + 1, 0, sizeof(int), st));
+  SC_CUDA(launch_copy_planes(cu, dl, dr, H, W, ws.E.p + E_PADL, pe, pstride, ws.flags.p, ws.flags.p + 1, st));
+  return launch_search(ws, ws.E.p, pe, H, W, seam_out, nullptr, cost_out, ws.flags.p + 1, st, pstride);
 }
 
 int sc_enlarge(const uint8_t *img, int H, int W, int C, int target_w, uint8_t *out, int32_t *cols_out, void *stream) {

@@ -27,11 +27,11 @@ DpShape dp_shape_for(int W) {
   return s;
 }
 
-template <int NW, int KT>
+template <int NW, int KT, bool FWD = false>
 __global__ void __launch_bounds__(Geo<NW, KT, true>::THREADS, 1) k_dp(DpArgs p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int S = (p.H + KS - 1) / KS;
-  search_init<NW, KT, true>(smem, S);
+  search_init<NW, KT, true, FILL_WARPS_MAX, FWD>(smem, S);
   // neighbours push into each other's halo buffers: every CTA's barriers must be initialised first
   cg::this_cluster().sync();
   SearchArgs a;
@@ -45,18 +45,19 @@ __global__ void __launch_bounds__(Geo<NW, KT, true>::THREADS, 1) k_dp(DpArgs p) 
   a.cost = p.cost;
   a.err = p.err;
   a.gated = (p.gate != nullptr) && (*p.gate & ERR_ENERGY_RANGE);
+  a.pstride = p.pstride;
   SearchState st;
-  seam_search<NW, KT, true>(a, smem, S, st);
+  seam_search<NW, KT, true, FILL_WARPS_MAX, FWD>(a, smem, S, st);
 }
 
-template <int NW, int KT>
+template <int NW, int KT, bool FWD = false>
 static cudaError_t launch_dp_shape(const DpArgs &a, int cs, cudaStream_t st) {
-  const size_t smem = search_plan<NW, KT, true>((a.H + KS - 1) / KS).total;
+  const size_t smem = search_plan<NW, KT, true, FILL_WARPS_MAX, FWD>((a.H + KS - 1) / KS).total;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_dp<NW, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaError_t e = cudaFuncSetAttribute(k_dp<NW, KT, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_dp<NW, KT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(k_dp<NW, KT, FWD>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -73,10 +74,18 @@ static cudaError_t launch_dp_shape(const DpArgs &a, int cs, cudaStream_t st) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_dp<NW, KT>, a);
+  return cudaLaunchKernelEx(&cfg, k_dp<NW, KT, FWD>, a);
 }
 
+// forward energy stages three planes per row: one shape, 4 warps x 16-row tiles (W <= 4096)
+int dp_forward_max_width() { return MAX_CLUSTER * Geo<4, 16, true>::OWC; }
+
 cudaError_t launch_dp(const DpArgs &a, cudaStream_t st) {
+  if (a.pstride > 0) {
+    const int cs = (a.W + Geo<4, 16, true>::OWC - 1) / Geo<4, 16, true>::OWC;
+    if (cs > MAX_CLUSTER) return cudaErrorInvalidValue;
+    return launch_dp_shape<4, 16, true>(a, cs < 1 ? 1 : cs, st);
+  }
   const DpShape s = dp_shape_for(a.W);
   if (s.cs > MAX_CLUSTER) return cudaErrorInvalidValue;
   if (s.nw == 4 && s.kt == 32) return launch_dp_shape<4, 32>(a, s.cs, st);

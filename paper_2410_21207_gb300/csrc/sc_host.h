@@ -15,7 +15,7 @@ int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
 int check_carve_args(const void *img, int H, int W, int C, int tw, int th, const void *out);
 // the cluster path of sc_carve on `st` (uses the stream's workspace)
 int carve_impl(const uint8_t *img, int H, int W, int C, int tw, int th, uint8_t *out, int32_t *seam_log,
-               int64_t *cost_log, cudaStream_t st);
+               int64_t *cost_log, cudaStream_t st, bool forward = false);
 int *device_error_word();
 
 struct BatchCfg {

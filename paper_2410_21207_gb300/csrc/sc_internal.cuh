@@ -54,6 +54,7 @@ struct DpArgs {
   int64_t *cost;       // nullable, out [1]
   int *err;            // device error word
   const int *gate;     // nullable: if *gate != 0 the search is skipped (energy range failure)
+  int64_t pstride = 0; // forward energy: elements between the CU, DL, DR planes (0: the e1 map)
 };
 
 // Launchers (enqueue on `st`; return cudaError_t of the launch).
@@ -66,7 +67,17 @@ cudaError_t launch_energy(const uint32_t *img, int pitch_img, int H, int W, uint
 cudaError_t launch_copy_energy(const uint16_t *src, int H, int W, uint16_t *E, int pitch_e, int *err, int *gate,
                                cudaStream_t st);
 cudaError_t launch_unpad_energy(const uint16_t *E, int pitch_e, int H, int W, uint16_t *dst, cudaStream_t st);
-cudaError_t launch_dp(const DpArgs &a, cudaStream_t st);
+// forward energy: the CU, DL, DR planes of a word image, or of a caller's planes (with the range
+// check and the unused border entries zeroed), plane p at E + p * pstride
+cudaError_t launch_forward(const uint32_t *img, int pitch, int H, int W, uint16_t *E, int pitch_e, int64_t pstride,
+                           cudaStream_t st);
+cudaError_t launch_copy_planes(const uint16_t *cu, const uint16_t *dl, const uint16_t *dr, int H, int W, uint16_t *E,
+                               int pitch_e, int64_t pstride, int *err, int *gate, cudaStream_t st);
+cudaError_t launch_refresh_fwd(const uint32_t *img, int pitch, uint16_t *E, int pe, int64_t pstride, int H, int W,
+                               const int32_t *seam, const int16_t *lists_in, int16_t *lists_out, int m, int *err,
+                               cudaStream_t st);
+cudaError_t launch_dp(const DpArgs &a, cudaStream_t st);   // forward energy when a.pstride > 0
+int dp_forward_max_width();                                 // widest map the forward search takes
 // n searches of H x W maps in one launch (one cluster each); dargs_dev is a device array
 cudaError_t launch_dp_multi(const DpArgs *dargs_dev, int n, int H, int W, cudaStream_t st);
 // how many H x W searches of launch_dp_multi are resident on the GPU at once

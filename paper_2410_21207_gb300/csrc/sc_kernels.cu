@@ -51,6 +51,41 @@ __global__ void k_energy(const uint32_t *__restrict__ img, int pitch, int H, int
   E[(int64_t)i * pe + j] = (uint16_t)energy_at(img, pitch, H, W, i, j);
 }
 
+// ---- forward energy: the CU, DL, DR planes (plane p at E + p * pstride) ----
+__global__ void k_forward(const uint32_t *__restrict__ img, int pitch, int H, int W, uint16_t *__restrict__ E, int pe,
+                          int64_t pstride) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j >= W || i >= H) return;
+  uint32_t cu, dl, dr;
+  forward_at([&](int r, int c) { return img[(int64_t)r * pitch + c]; }, W, i, j, cu, dl, dr);
+  E[(int64_t)i * pe + j] = (uint16_t)cu;
+  E[pstride + (int64_t)i * pe + j] = (uint16_t)dl;
+  E[2 * pstride + (int64_t)i * pe + j] = (uint16_t)dr;
+}
+
+// ---- caller forward planes -> padded layout. DL in row 0 and column 0 and DR in row 0 and the
+// last column are never used (no such predecessor) and are stored as 0; the range check bounds
+// every cell's CU + max(DL, DR). ----
+__global__ void k_copy_planes(const uint16_t *__restrict__ cu, const uint16_t *__restrict__ dl,
+                              const uint16_t *__restrict__ dr, int H, int W, uint16_t *__restrict__ E, int pe,
+                              int64_t pstride, uint32_t limit, int *err, int *gate) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j >= W || i >= H) return;
+  const int64_t q = (int64_t)i * W + j;
+  const uint32_t u = cu[q];
+  const uint32_t l = (i >= 1 && j >= 1) ? dl[q] : 0u;
+  const uint32_t r = (i >= 1 && j + 1 < W) ? dr[q] : 0u;
+  E[(int64_t)i * pe + j] = (uint16_t)u;
+  E[pstride + (int64_t)i * pe + j] = (uint16_t)l;
+  E[2 * pstride + (int64_t)i * pe + j] = (uint16_t)r;
+  if (u + (l > r ? l : r) > limit) {
+    atomicOr(err, ERR_ENERGY_RANGE);
+    atomicOr(gate, ERR_ENERGY_RANGE);
+  }
+}
+
 // ---- caller energy -> padded layout, with the range check of the 24-bit cost field ----
 __global__ void k_copy_energy(const uint16_t *__restrict__ src, int H, int W, uint16_t *__restrict__ E, int pe,
                               uint32_t limit, int *err, int *gate) {
@@ -81,6 +116,16 @@ __global__ void k_refresh(const uint32_t *__restrict__ img, int pitch, uint16_t 
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < H; i += warps)
     if (!refresh_row(img, pitch, E, pe, H, W, seam, lists_in, lists_out, m, i, lane) && lane == 0)
+      atomicOr(err, ERR_BAD_SEAM);
+}
+
+__global__ void k_refresh_fwd(const uint32_t *__restrict__ img, int pitch, uint16_t *__restrict__ E, int pe,
+                              int64_t pstride, int H, int W, const int32_t *__restrict__ seam,
+                              const int16_t *__restrict__ lists_in, int16_t *__restrict__ lists_out, int m, int *err) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < H; i += warps)
+    if (!refresh_row_fwd(img, pitch, E, pe, pstride, H, W, seam, lists_in, lists_out, m, i, lane) && lane == 0)
       atomicOr(err, ERR_BAD_SEAM);
 }
 
@@ -132,6 +177,21 @@ cudaError_t launch_copy_energy(const uint16_t *src, int H, int W, uint16_t *E, i
   return cudaGetLastError();
 }
 
+cudaError_t launch_forward(const uint32_t *img, int pitch, int H, int W, uint16_t *E, int pe, int64_t pstride,
+                           cudaStream_t st) {
+  dim3 grid((W + 127) / 128, H);
+  k_forward<<<grid, 128, 0, st>>>(img, pitch, H, W, E, pe, pstride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_planes(const uint16_t *cu, const uint16_t *dl, const uint16_t *dr, int H, int W, uint16_t *E,
+                               int pe, int64_t pstride, int *err, int *gate, cudaStream_t st) {
+  const uint32_t limit = (uint32_t)((((uint64_t)1 << 24) - 1) / (uint64_t)H);
+  dim3 grid((W + 127) / 128, H);
+  k_copy_planes<<<grid, 128, 0, st>>>(cu, dl, dr, H, W, E, pe, pstride, limit, err, gate);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_unpad_energy(const uint16_t *E, int pe, int H, int W, uint16_t *dst, cudaStream_t st) {
   dim3 grid((W + 127) / 128, H);
   k_unpad_energy<<<grid, 128, 0, st>>>(E, pe, H, W, dst);
@@ -148,6 +208,17 @@ cudaError_t launch_refresh(const uint32_t *img, int pitch, uint16_t *E, int pe, 
   int blocks = (H + warps_per_block - 1) / warps_per_block;
   if (blocks > 152 * 8) blocks = 152 * 8;
   k_refresh<<<blocks, warps_per_block * 32, 0, st>>>(img, pitch, E, pe, H, W, seam, lists_in, lists_out, m, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refresh_fwd(const uint32_t *img, int pitch, uint16_t *E, int pe, int64_t pstride, int H, int W,
+                               const int32_t *seam, const int16_t *lists_in, int16_t *lists_out, int m, int *err,
+                               cudaStream_t st) {
+  const int warps_per_block = 8;
+  int blocks = (H + warps_per_block - 1) / warps_per_block;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_refresh_fwd<<<blocks, warps_per_block * 32, 0, st>>>(img, pitch, E, pe, pstride, H, W, seam, lists_in, lists_out,
+                                                          m, err);
   return cudaGetLastError();
 }
 

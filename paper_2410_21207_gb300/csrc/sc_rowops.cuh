@@ -201,4 +201,74 @@ __device__ __forceinline__ bool refresh_row(const uint32_t *img, int pitch, uint
   return true;
 }
 
+// ---- forward energy ----
+// The three cost planes of pixel (i, j) of a rows x cols word image: CU = |P(i,j+1) - P(i,j-1)|
+// (0 at the first and last column), DL = |P(i-1,j) - P(i,j-1)| (0 in row 0 and column 0),
+// DR = |P(i-1,j) - P(i,j+1)| (0 in row 0 and the last column), each summed over the channels.
+// pix(r, c) returns the word of pixel (r, c) (r, c inside the image).
+template <typename Pix>
+__device__ __forceinline__ void forward_at(Pix pix, int cols, int i, int j, uint32_t &cu, uint32_t &dl, uint32_t &dr) {
+  const bool left = j >= 1, right = j + 1 < cols;
+  const uint32_t pl = left ? pix(i, j - 1) : 0u, pr = right ? pix(i, j + 1) : 0u;
+  cu = (left && right) ? sad4(pr, pl) : 0u;
+  dl = dr = 0u;
+  if (i >= 1) {
+    const uint32_t up = pix(i - 1, j);
+    if (left) dl = sad4(up, pl);
+    if (right) dr = sad4(up, pr);
+  }
+}
+
+// The forward-energy planes at the new columns s-1 and s of row i after removing `seam` (the
+// other columns are shifted copies: the dirty set of the e1 refresh holds for all three planes),
+// the image read through the pending-removal lists. out[plane] = value(s-1) | value(s) << 16.
+__device__ __forceinline__ void patch_row_lazy_fwd(const uint32_t *img, int pitch, int H, int W, const int32_t *seam,
+                                                   const int16_t *lists, int m, int i, uint32_t (&out)[3], bool *bad) {
+  const int Wn = W - 1;
+  const int s = seam[i];
+  out[0] = out[1] = out[2] = 0u;
+  if (s < 0 || s >= W) {
+    *bad = true;
+    return;
+  }
+  auto pix = [&](int r, int j) -> uint32_t {
+    const int x = j + (j >= seam[r] ? 1 : 0);                    // column in the width-W image
+    return img[(int64_t)r * pitch + lazy_map(lists + (int64_t)r * RPEND, m, x)];
+  };
+  uint32_t cu, dl, dr;
+  if (s >= 1) {
+    forward_at(pix, Wn, i, s - 1, cu, dl, dr);
+    out[0] = cu; out[1] = dl; out[2] = dr;
+  }
+  if (s <= Wn - 1) {
+    forward_at(pix, Wn, i, s, cu, dl, dr);
+    out[0] |= cu << 16; out[1] |= dl << 16; out[2] |= dr << 16;
+  }
+}
+
+// refresh_row for the three forward-energy planes (plane p at E + p * pstride)
+__device__ __forceinline__ bool refresh_row_fwd(const uint32_t *img, int pitch, uint16_t *E, int pe, int64_t pstride,
+                                                int H, int W, const int32_t *seam, const int16_t *lists_in,
+                                                int16_t *lists_out, int m, int i, int lane) {
+  const int s = seam[i];
+  if (s < 0 || s >= W) return false;
+  uint32_t pr[3] = {0u, 0u, 0u};
+  if (lane == 0) {
+    bool bad = false;
+    patch_row_lazy_fwd(img, pitch, H, W, seam, lists_in, m, i, pr, &bad);
+    list_insert(lists_in + (int64_t)i * RPEND, lists_out + (int64_t)i * RPEND, m, s);
+  }
+#pragma unroll
+  for (int pl = 0; pl < 3; ++pl) {
+    const uint32_t v = __shfl_sync(0xffffffffu, pr[pl], 0);
+    uint16_t *er = E + pl * pstride + (int64_t)i * pe;
+    shift_row_u16(er, s, W, lane);
+    if (lane == 0) {
+      if (s >= 1) er[s - 1] = (uint16_t)(v & 0xFFFFu);
+      if (s <= W - 2) er[s] = (uint16_t)(v >> 16);
+    }
+  }
+  return true;
+}
+
 }  // namespace sc

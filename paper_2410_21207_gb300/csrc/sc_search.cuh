@@ -30,6 +30,10 @@
 //     and per-super-tile bookkeeping runs after the tile, on its last row (the only row of a full
 //     tile where it can occur, since KS is a multiple of KT).
 // The result is Algorithm 3's seam exactly (leftmost ties, leftmost last-row minimum).
+// With FWD (forward energy) the map has three planes, CU, DL and DR, and a cell's cost depends on
+// the direction it is reached from: M(i,j) = CU(i,j) + min(M(i-1,j-1) + DL(i,j), M(i-1,j),
+// M(i-1,j+1) + DR(i,j)). Optimal predecessors still never cross (a crossing pair would need
+// DL + DR < 0), so the ancestor keys keep their meaning; the planes are staged side by side.
 #pragma once
 #include <cooperative_groups.h>
 #include <type_traits>
@@ -63,7 +67,7 @@ struct SearchPlan {
   size_t bnd, hbuf, anc, wmin, cmin, jb, misc, fdir, ring, bars, total;
 };
 
-template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX>
+template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false>
 __host__ __device__ inline SearchPlan search_plan(int S) {
   using G = Geo<NW, KT, CL, FWM>;
   SearchPlan p;
@@ -76,7 +80,7 @@ __host__ __device__ inline SearchPlan search_plan(int S) {
   p.jb = o;   o += (size_t)(S + 1) * 4;  o = (o + 15) & ~(size_t)15;
   p.misc = o; o += 16;
   p.fdir = o; o += (size_t)G::FW * KS * 32 * 2;  o = (o + 15) & ~(size_t)15;
-  p.ring = o; o += (size_t)NSLOT * KT * G::BW * 2;  o = (o + 15) & ~(size_t)15;
+  p.ring = o; o += (size_t)NSLOT * (FWD ? 3 : 1) * KT * G::BW * 2;  o = (o + 15) & ~(size_t)15;
   p.bars = o; o += (size_t)(2 * NSLOT + 2) * 8;   // full[NSLOT], empty[NSLOT], halo[2]
   p.total = (o + 15) & ~(size_t)15;
   return p;
@@ -92,6 +96,7 @@ struct SearchArgs {
   int64_t *cost;       // nullable, out [1]
   int *err;            // device error word
   bool gated;          // skip the search (energy range failure)
+  int64_t pstride;     // forward energy: elements from one cost plane (CU, DL, DR) to the next
 };
 
 // Running counters of the mbarrier phases, identical in every thread of the CTA.
@@ -163,11 +168,41 @@ __device__ __forceinline__ void dp_rows(uint32_t (&k)[V], const uint16_t *er, co
   }
 }
 
+// One forward-energy row: keys k (previous row) -> next row; cu, dl, dr: 4 x uint16 each.
+__device__ __forceinline__ void dp_row_fwd(uint32_t (&k)[V], uint2 cu, uint2 dl, uint2 dr, const uint32_t (&oobm)[V]) {
+  const uint32_t L = __shfl_up_sync(0xffffffffu, k[V - 1], 1);
+  const uint32_t R = __shfl_down_sync(0xffffffffu, k[0], 1);
+  const uint32_t n0 = (min3u(L + lo8(dl.x), k[0], k[1] + lo8(dr.x)) + lo8(cu.x)) | oobm[0];
+  const uint32_t n1 = (min3u(k[0] + hi8(dl.x), k[1], k[2] + hi8(dr.x)) + hi8(cu.x)) | oobm[1];
+  const uint32_t n2 = (min3u(k[1] + lo8(dl.y), k[2], k[3] + lo8(dr.y)) + lo8(cu.y)) | oobm[2];
+  const uint32_t n3 = (min3u(k[2] + hi8(dl.y), k[3], R + hi8(dr.y)) + hi8(cu.y)) | oobm[3];
+  k[0] = n0; k[1] = n1; k[2] = n2; k[3] = n3;
+}
+
+// KT forward-energy rows of a full tile; the three planes are KT rows apart in the staging ring.
+template <int KT, int BW, bool MASK>
+__device__ __forceinline__ void dp_rows_fwd(uint32_t (&k)[V], const uint16_t *er, const uint32_t (&oobm)[V]) {
+  constexpr uint32_t Z[V] = {0u, 0u, 0u, 0u};
+  constexpr int PL = KT * BW;
+  uint2 a0 = *reinterpret_cast<const uint2 *>(er), a1 = *reinterpret_cast<const uint2 *>(er + PL),
+        a2 = *reinterpret_cast<const uint2 *>(er + 2 * PL);
+#pragma unroll
+  for (int r = 0; r < KT; ++r) {
+    const uint2 c0 = a0, c1 = a1, c2 = a2;
+    if (r + 1 < KT) {
+      a0 = *reinterpret_cast<const uint2 *>(er + (r + 1) * BW);
+      a1 = *reinterpret_cast<const uint2 *>(er + PL + (r + 1) * BW);
+      a2 = *reinterpret_cast<const uint2 *>(er + 2 * PL + (r + 1) * BW);
+    }
+    dp_row_fwd(k, c0, c1, c2, MASK ? oobm : Z);
+  }
+}
+
 // Initialise the staging and halo mbarriers (thread 0; the caller then synchronises the CTA, and
 // the cluster when CL).
-template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX>
+template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false>
 __device__ inline void search_init(unsigned char *smem, int S) {
-  const SearchPlan plan = search_plan<NW, KT, CL, FWM>(S);
+  const SearchPlan plan = search_plan<NW, KT, CL, FWM, FWD>(S);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + plan.bars);
   uint64_t *empty = full + NSLOT;
   uint64_t *hbar = empty + NSLOT;
@@ -189,8 +224,9 @@ __device__ __forceinline__ void group_sync() {
 
 // The search. Every thread of the CTA (of every CTA of the cluster when CL) calls it with the same
 // arguments; `Smax` is the super-tile count the shared-memory plan was sized for.
-template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX>
+template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false>
 __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, SearchState &st) {
+  constexpr int NP = FWD ? 3 : 1;   // cost planes staged per row
   using G = Geo<NW, KT, CL, FWM>;
   constexpr int Q = G::Q, BW = G::BW, OWC = G::OWC, K2E = G::K2E;
   const int rank = CL ? (int)cg::this_cluster().block_rank() : 0;
@@ -199,7 +235,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   const bool producer = (warp == NW);
   const int H = p.H, W = p.W;
   const int S = (H + KS - 1) / KS;
-  const SearchPlan plan = search_plan<NW, KT, CL, FWM>(Smax);
+  const SearchPlan plan = search_plan<NW, KT, CL, FWM, FWD>(Smax);
   uint32_t *bnd = reinterpret_cast<uint32_t *>(smem + plan.bnd);
   uint32_t *hbuf = reinterpret_cast<uint32_t *>(smem + plan.hbuf);
   uint8_t *ancT = reinterpret_cast<uint8_t *>(smem + plan.anc);
@@ -237,6 +273,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   // fields used inside the loops, held in registers (stores through the map pointers could
   // otherwise force reloads of the argument struct)
   const int pitch_e = p.pitch_e;
+  const int64_t pstride = FWD ? p.pstride : 0;
   uint32_t *const Mrow = p.Mrow;
 
   if (producer) {
@@ -250,11 +287,14 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
       }
       const int rbeg = tt * KT;
       const int nrows = (H - rbeg < KT) ? H - rbeg : KT;
-      if (lane == 0) mbar_arrive_expect_tx(&full[slot], (uint32_t)nrows * ROW_BYTES);
+      if (lane == 0) mbar_arrive_expect_tx(&full[slot], (uint32_t)(NP * nrows) * ROW_BYTES);
       __syncwarp();
-      if (lane < nrows)
-        bulk_g2s(ring + (size_t)(slot * KT + lane) * BW, Estage + (size_t)(rbeg + lane) * pitch_e, ROW_BYTES,
-                 &full[slot]);
+      if (lane < nrows) {
+#pragma unroll
+        for (int pl = 0; pl < NP; ++pl)
+          bulk_g2s(ring + (size_t)((slot * NP + pl) * KT + lane) * BW,
+                   Estage + pl * pstride + (size_t)(rbeg + lane) * pitch_e, ROW_BYTES, &full[slot]);
+      }
     }
   } else if (!active) {
     // outside the image: release every slot at once and keep the barrier count
@@ -281,7 +321,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
         }
         // test the next tile's staging now: the answer is needed only at the next tile boundary
         ready = more && mbar_test_wait(&full[(g + 1) % NSLOT], ((g + 1) / NSLOT) & 1u);
-        const uint16_t *er = ring + (size_t)slot * KT * BW + bidx0;
+        const uint16_t *er = ring + (size_t)slot * NP * KT * BW + bidx0;
         if (t > 0) {
           // window of the previous row from the boundary buffer (relative ancestors -> warp frame).
           // At a new super-tile every cell becomes its own ancestor; the old ancestor field is
@@ -299,7 +339,8 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
           // full tile: KT branch-free rows (the energies of the next rows are loaded ahead of
           // the row that needs them, off the dependent chain); bookkeeping only where a
           // super-tile or the image ends on its last row
-          dp_rows<KT, BW, EDGE>(k, er, oobm);
+          if (FWD) dp_rows_fwd<KT, BW, EDGE>(k, er, oobm);
+          else dp_rows<KT, BW, EDGE>(k, er, oobm);
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[slot]);   // this warp is done with the staged rows
           if (((r0 + KT) % KS) == 0 || r0 + KT == H)
@@ -309,12 +350,15 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
           for (int r = 0; r < KT; ++r) {
             const int i = r0 + r;
             if (i >= H) break;
-            const uint2 ev = *reinterpret_cast<const uint2 *>(er + r * BW);
+            const uint2 ev = *reinterpret_cast<const uint2 *>(er + r * BW);   // CU with FWD
             if (i == 0) {
               k[0] = (lo8(ev.x) | own_a) | oobm[0];
               k[1] = (hi8(ev.x) | (own_a + 1u)) | oobm[1];
               k[2] = (lo8(ev.y) | (own_a + 2u)) | oobm[2];
               k[3] = (hi8(ev.y) | (own_a + 3u)) | oobm[3];
+            } else if (FWD) {
+              dp_row_fwd(k, ev, *reinterpret_cast<const uint2 *>(er + KT * BW + r * BW),
+                         *reinterpret_cast<const uint2 *>(er + 2 * KT * BW + r * BW), oobm);
             } else {
               dp_row(k, ev, oobm);
             }
@@ -421,7 +465,8 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
     int x0 = jb0[s] - 128;
     x0 -= ((x0 % 8) + 8) % 8;
     for (int i = s * KS + lane; i < s * KS + KS && i < H; i += 32)
-      bulk_prefetch_l2(Ef + (size_t)i * pitch_e + x0, FILL_W * 2);
+#pragma unroll
+      for (int pl = 0; pl < NP; ++pl) bulk_prefetch_l2(Ef + pl * pstride + (size_t)i * pitch_e + x0, FILL_W * 2);
   };
   if (ok && warp < G::FW) prefetch_window(warp * cs + rank);
   for (int s = warp * cs + rank; ok && warp < G::FW && s < S; s += G::FW * cs) {
@@ -447,32 +492,42 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) m[u] |= oob[u];
-    // rows first..re-1 in chunks of 4 with the next chunk's energies loaded ahead
-    constexpr int CH = 4;
-    uint4 eb0[CH], eb1[CH];
-    auto load_chunk = [&](uint4 (&eb)[CH], int rbeg) {
+    // rows first..re-1 in chunks with the next chunk's energies loaded ahead
+    constexpr int CH = FWD ? 2 : 4;
+    uint4 eb0[NP][CH], eb1[NP][CH];
+    auto load_chunk = [&](uint4 (&eb)[NP][CH], int rbeg) {
 #pragma unroll
       for (int r = 0; r < CH; ++r) {
         const int i = rbeg + r;
-        if (i < re) eb[r] = *reinterpret_cast<const uint4 *>(Ef + (size_t)i * pitch_e + xc);
+#pragma unroll
+        for (int pl = 0; pl < NP; ++pl)
+          if (i < re) eb[pl][r] = *reinterpret_cast<const uint4 *>(Ef + pl * pstride + (size_t)i * pitch_e + xc);
       }
     };
-    auto run_chunk = [&](const uint4 (&eb)[CH], int rbeg) {
+    auto unpack8 = [](const uint4 &v, uint32_t (&x)[8]) {
+      x[0] = v.x & 0xFFFFu; x[1] = v.x >> 16; x[2] = v.y & 0xFFFFu; x[3] = v.y >> 16;
+      x[4] = v.z & 0xFFFFu; x[5] = v.z >> 16; x[6] = v.w & 0xFFFFu; x[7] = v.w >> 16;
+    };
+    auto run_chunk = [&](const uint4 (&eb)[NP][CH], int rbeg) {
 #pragma unroll
       for (int r = 0; r < CH; ++r) {
         const int i = rbeg + r;
         if (i >= re) break;
-        const uint32_t ee[8] = {eb[r].x & 0xFFFFu, eb[r].x >> 16, eb[r].y & 0xFFFFu, eb[r].y >> 16,
-                                eb[r].z & 0xFFFFu, eb[r].z >> 16, eb[r].w & 0xFFFFu, eb[r].w >> 16};
+        uint32_t ee[8], dl[8] = {0, 0, 0, 0, 0, 0, 0, 0}, dr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        unpack8(eb[0][r], ee);
+        if (FWD) {
+          unpack8(eb[NP > 1 ? 1 : 0][r], dl);
+          unpack8(eb[NP > 2 ? 2 : 0][r], dr);
+        }
         const uint32_t L = __shfl_up_sync(0xffffffffu, m[7], 1);
         const uint32_t R = __shfl_down_sync(0xffffffffu, m[0], 1);
         uint32_t nm[8];
         uint32_t dirs = 0;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const uint32_t a = (u == 0) ? L : m[u - 1];
+          const uint32_t a = ((u == 0) ? L : m[u - 1]) + dl[u];
           const uint32_t b = m[u];
-          const uint32_t c = (u == 7) ? R : m[u + 1];
+          const uint32_t c = ((u == 7) ? R : m[u + 1]) + dr[u];
           const uint32_t mn = min3u(a, b, c);
           const uint32_t dd = (a == mn) ? 0u : ((b == mn) ? 1u : 2u);
           dirs |= dd << (2 * u);
