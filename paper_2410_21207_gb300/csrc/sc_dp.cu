@@ -34,6 +34,9 @@ __global__ void __launch_bounds__(Geo<NW, KT, true>::THREADS, 1) k_dp(DpArgs p) 
   search_init<NW, KT, true, FILL_WARPS_MAX, FWD>(smem, S);
   // neighbours push into each other's halo buffers: every CTA's barriers must be initialised first
   cg::this_cluster().sync();
+  // the set-up above overlaps the previous kernel of the seam loop; its results are read below
+  pdl_launch_dependents();
+  pdl_wait_prerequisites();
   SearchArgs a;
   a.E = p.E;
   a.pitch_e = p.pitch_e;
@@ -67,13 +70,15 @@ static cudaError_t launch_dp_shape(const DpArgs &a, int cs, cudaStream_t st) {
   cfg.blockDim = dim3(Geo<NW, KT, true>::THREADS);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = cs;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // may start before its predecessor ends
+  at[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, k_dp<NW, KT, FWD>, a);
 }
 

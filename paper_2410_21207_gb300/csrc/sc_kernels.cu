@@ -114,6 +114,8 @@ __global__ void k_refresh(const uint32_t *__restrict__ img, int pitch, uint16_t 
                           int16_t *__restrict__ lists_out, int m, int *err) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
+  pdl_launch_dependents();
+  pdl_wait_prerequisites();   // the seam of the search that precedes this launch
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < H; i += warps)
     if (!refresh_row(img, pitch, E, pe, H, W, seam, lists_in, lists_out, m, i, lane) && lane == 0)
       atomicOr(err, ERR_BAD_SEAM);
@@ -124,6 +126,8 @@ __global__ void k_refresh_fwd(const uint32_t *__restrict__ img, int pitch, uint1
                               const int16_t *__restrict__ lists_in, int16_t *__restrict__ lists_out, int m, int *err) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
+  pdl_launch_dependents();
+  pdl_wait_prerequisites();
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < H; i += warps)
     if (!refresh_row_fwd(img, pitch, E, pe, pstride, H, W, seam, lists_in, lists_out, m, i, lane) && lane == 0)
       atomicOr(err, ERR_BAD_SEAM);
@@ -133,11 +137,30 @@ __global__ void k_compact_lazy(uint32_t *__restrict__ img, int pitch, int H, int
                                int m) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
+  pdl_launch_dependents();
+  pdl_wait_prerequisites();
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < H; i += warps)
     compact_row_lazy(img + (int64_t)i * pitch, lists + (int64_t)i * RPEND, m, w, lane);
 }
 
 // ---- launchers ----
+// launch as a programmatic dependent of the previous kernel on the stream (the kernels of the seam
+// loop wait for their predecessor with griddepcontrol.wait before touching its results)
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), int blocks, int threads, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 static int grid_for(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   if (b > 152 * 64) b = 152 * 64;
@@ -207,8 +230,8 @@ cudaError_t launch_refresh(const uint32_t *img, int pitch, uint16_t *E, int pe, 
   const int warps_per_block = 8;
   int blocks = (H + warps_per_block - 1) / warps_per_block;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  k_refresh<<<blocks, warps_per_block * 32, 0, st>>>(img, pitch, E, pe, H, W, seam, lists_in, lists_out, m, err);
-  return cudaGetLastError();
+  return launch_pdl(k_refresh, blocks, warps_per_block * 32, st, img, pitch, E, pe, H, W, seam, lists_in, lists_out, m,
+                    err);
 }
 
 cudaError_t launch_refresh_fwd(const uint32_t *img, int pitch, uint16_t *E, int pe, int64_t pstride, int H, int W,
@@ -217,17 +240,15 @@ cudaError_t launch_refresh_fwd(const uint32_t *img, int pitch, uint16_t *E, int 
   const int warps_per_block = 8;
   int blocks = (H + warps_per_block - 1) / warps_per_block;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  k_refresh_fwd<<<blocks, warps_per_block * 32, 0, st>>>(img, pitch, E, pe, pstride, H, W, seam, lists_in, lists_out,
-                                                          m, err);
-  return cudaGetLastError();
+  return launch_pdl(k_refresh_fwd, blocks, warps_per_block * 32, st, img, pitch, E, pe, pstride, H, W, seam, lists_in,
+                    lists_out, m, err);
 }
 
 cudaError_t launch_compact_lazy(uint32_t *img, int pitch, int H, int w, const int16_t *lists, int m, cudaStream_t st) {
   const int warps_per_block = 8;
   int blocks = (H + warps_per_block - 1) / warps_per_block;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  k_compact_lazy<<<blocks, warps_per_block * 32, 0, st>>>(img, pitch, H, w, lists, m);
-  return cudaGetLastError();
+  return launch_pdl(k_compact_lazy, blocks, warps_per_block * 32, st, img, pitch, H, w, lists, m);
 }
 
 }  // namespace sc

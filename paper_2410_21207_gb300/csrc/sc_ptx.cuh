@@ -103,6 +103,12 @@ __device__ __forceinline__ void st_async_v4(uint32_t remote_addr, uint4 v, uint3
                : "memory");
 }
 
+// Programmatic dependent launch: let the next kernel on the stream be scheduled now (its
+// prologue overlaps this kernel), and wait until the previous kernel has completed and its memory
+// is visible (returns at once when this kernel was not launched as a dependent).
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait_prerequisites() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // barrier over the first `nthreads` threads of the CTA (named barrier 1)
 __device__ __forceinline__ void named_bar_sync(uint32_t nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
