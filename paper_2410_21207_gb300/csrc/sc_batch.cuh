@@ -47,7 +47,11 @@ __device__ void batch_seam_pass(const BatchItem &it, uint32_t *words, int rows, 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   int16_t *lb[2] = {it.lists, it.lists + (size_t)rows * RPEND};
   // the staging ring is idle between searches: it holds the rows' refreshed pairs
-  uint32_t *pairs = reinterpret_cast<uint32_t *>(smem + search_plan<NW, KT, false>(Smax).ring);
+  const SearchPlan plan = search_plan<NW, KT, false>(Smax);
+  uint32_t *pairs = reinterpret_cast<uint32_t *>(smem + plan.ring);
+  const size_t pair_bytes = ((size_t)rows * 4 + 15) & ~(size_t)15;
+  uint16_t *sbuf = reinterpret_cast<uint16_t *>(smem + plan.ring + pair_bytes);
+  const int sbuf_elems = (int)(((plan.bars - plan.ring - pair_bytes) / nwarps) & ~(size_t)15) / 2;
   uint16_t *const Ecur = it.E + E_PADL;
   int cur = 0, m = 0;
   for (int t = 0; t < count; ++t) {
@@ -72,18 +76,10 @@ __device__ void batch_seam_pass(const BatchItem &it, uint32_t *words, int rows, 
     }
     if (bad) atomicOr(err, ERR_BAD_SEAM);
     __syncthreads();
-    // energy rows compacted past the seam in place, the pair at the new columns s-1 and s
-    for (int i = warp; i < rows; i += nwarps) {
-      const int s = it.seam[i];
-      if (s < 0 || s >= w) continue;
-      uint16_t *er = Ecur + (size_t)i * it.pe;
-      shift_row_u16(er, s, w, lane);
-      if (lane == 0) {
-        const uint32_t pr = pairs[i];
-        if (s >= 1) er[s - 1] = (uint16_t)(pr & 0xFFFFu);
-        if (s <= w - 2) er[s] = (uint16_t)(pr >> 16);
-      }
-    }
+    // energy rows compacted past the seam in place, the pair at the new columns s-1 and s; the
+    // tails go through the rest of the idle ring, one buffer per warp
+    shift_rows_staged(Ecur, it.pe, rows, w, it.seam, pairs, warp, nwarps, lane, sbuf + (size_t)warp * sbuf_elems,
+                      sbuf_elems);
     cur ^= 1;
     fence_proxy_async_global();   // the next search stages the compacted energy rows with TMA
     __syncthreads();

@@ -103,6 +103,14 @@ __device__ __forceinline__ void st_async_v4(uint32_t remote_addr, uint4 v, uint3
                : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned), completed by cp_async_wait_all
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src_gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src_gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Programmatic dependent launch: let the next kernel on the stream be scheduled now (its
 // prologue overlaps this kernel), and wait until the previous kernel has completed and its memory
 // is visible (returns at once when this kernel was not launched as a dependent).

@@ -5,6 +5,8 @@
 #pragma once
 #include <cstdint>
 
+#include "sc_ptx.cuh"
+
 namespace sc {
 
 // sum over the four bytes of |a_b - b_b|
@@ -199,6 +201,115 @@ __device__ __forceinline__ bool refresh_row(const uint32_t *img, int pitch, uint
     if (s <= W - 2) er[s] = (uint16_t)(p >> 16);
   }
   return true;
+}
+
+// The energy shift of every row this warp owns (rows warp, warp + nwarps, ...), each followed by
+// its refreshed pair (pairs[row]: e(s-1) | e(s) << 16). The tails of as many rows as fit the
+// warp's shared-memory buffer (buf_elems uint16, 16-byte aligned) are copied in with cp.async, all
+// in flight at once, then written back one element to the left; eight lanes work on each row, four
+// rows at a time, so no per-row chain of dependent steps is paid row after row. Rows whose seam is
+// out of range are skipped (the caller records the error).
+__device__ inline void shift_rows_staged(uint16_t *E, int pe, int rows, int w, const int32_t *seam,
+                                         const uint32_t *pairs, int warp, int nwarps, int lane, uint16_t *buf,
+                                         int buf_elems) {
+  const int sub = lane >> 3, sl = lane & 7;
+  const int c_last = (w - 2) >> 3;   // the chunk holding the new last column
+  // the warp's rows in blocks of 32: one seam load per lane, read back with shuffles
+  for (int blk = warp; blk < rows; blk += 32 * nwarps) {
+    const int my_row = blk + lane * nwarps;
+    const int my_s = my_row < rows ? seam[my_row] : -1;
+    const int nb = min(32, (rows - blk + nwarps - 1) / nwarps);
+    int k = 0;
+    while (k < nb) {
+      // a group of rows whose tails fit the buffer; lane q records group row q (block index, offset)
+      int info_k = 0, info_off = 0, ng = 0, used = 0;
+      while (k < nb) {
+        const int i = blk + k * nwarps;
+        const int s = __shfl_sync(0xffffffffu, my_s, k);
+        if (s < 0 || s >= w) { ++k; continue; }
+        uint16_t *er = E + (size_t)i * pe;
+        if (s >= w - 1) {   // nothing to shift: only the left refreshed value
+          if (lane == 0 && s >= 1) er[s - 1] = (uint16_t)(pairs[i] & 0xFFFFu);
+          ++k;
+          continue;
+        }
+        const int need = 8 * (c_last - (s >> 3) + 2);   // the tail's chunks, plus the one after it
+        if (need > buf_elems) {   // a tail longer than the buffer: shifted in place, chunk by chunk
+          if (ng > 0) break;
+          shift_row_u16(er, s, w, lane);
+          __syncwarp();
+          if (lane == 0) {
+            if (s >= 1) er[s - 1] = (uint16_t)(pairs[i] & 0xFFFFu);
+            er[s] = (uint16_t)(pairs[i] >> 16);
+          }
+          ++k;
+          continue;
+        }
+        if (ng == 32 || used + need > buf_elems) break;
+        if (lane == ng) {
+          info_k = k;
+          info_off = used;
+        }
+        used += need;
+        ++ng;
+        ++k;
+      }
+      // copy in: eight lanes per row, four rows at a time
+      for (int q0 = 0; q0 < ng; q0 += 4) {
+        const int q = q0 + sub, qq = q < ng ? q : ng - 1;
+        const int kk = __shfl_sync(0xffffffffu, info_k, qq);
+        const int off = __shfl_sync(0xffffffffu, info_off, qq);
+        const int s = __shfl_sync(0xffffffffu, my_s, kk);
+        if (q < ng) {
+          const uint16_t *er = E + (size_t)(blk + kk * nwarps) * pe;
+          const int c_lo = s >> 3, nch = c_last - c_lo + 2;
+          for (int c = sl; c < nch; c += 8) cp_async16(buf + off + 8 * c, er + 8 * (c_lo + c));
+        }
+      }
+      cp_async_wait_all();
+      __syncwarp();
+      // write back shifted, the first chunk keeping its elements left of s, then the refreshed pair
+      for (int q0 = 0; q0 < ng; q0 += 4) {
+        const int q = q0 + sub, qq = q < ng ? q : ng - 1;
+        const int kk = __shfl_sync(0xffffffffu, info_k, qq);
+        const int off = __shfl_sync(0xffffffffu, info_off, qq);
+        const int s = __shfl_sync(0xffffffffu, my_s, kk);
+        if (q < ng) {
+          const int r = blk + kk * nwarps;
+          uint16_t *er = E + (size_t)r * pe;
+          const uint16_t *b = buf + off;
+          const int c_lo = s >> 3;
+          for (int c = c_lo + sl; c <= c_last; c += 8) {
+            const uint4 x = *reinterpret_cast<const uint4 *>(b + 8 * (c - c_lo));
+            const uint32_t nx = b[8 * (c - c_lo) + 8];
+            uint4 o;
+            o.x = __funnelshift_r(x.x, x.y, 16);
+            o.y = __funnelshift_r(x.y, x.z, 16);
+            o.z = __funnelshift_r(x.z, x.w, 16);
+            o.w = __funnelshift_r(x.w, nx, 16);
+            if (c == c_lo) {
+              const int keep = s - 8 * c;   // leading elements of this chunk that stay
+              auto merge = [keep](uint32_t in, uint32_t sh, int j) {
+                const uint32_t m = (2 * j < keep ? 0x0000FFFFu : 0u) | (2 * j + 1 < keep ? 0xFFFF0000u : 0u);
+                return (in & m) | (sh & ~m);
+              };
+              o.x = merge(x.x, o.x, 0);
+              o.y = merge(x.y, o.y, 1);
+              o.z = merge(x.z, o.z, 2);
+              o.w = merge(x.w, o.w, 3);
+            }
+            *reinterpret_cast<uint4 *>(er + 8 * c) = o;
+            if (c == c_lo) {   // this lane wrote the chunk holding s: the refreshed pair goes over it
+              const uint32_t pr = pairs[r];
+              if (s >= 1) er[s - 1] = (uint16_t)(pr & 0xFFFFu);
+              if (s <= w - 2) er[s] = (uint16_t)(pr >> 16);
+            }
+          }
+        }
+      }
+      __syncwarp();   // the buffer is reused by the next group
+    }
+  }
 }
 
 // ---- forward energy ----

@@ -492,8 +492,10 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) m[u] |= oob[u];
-    // rows first..re-1 in chunks with the next chunk's energies loaded ahead
-    constexpr int CH = FWD ? 2 : 4;
+    // rows first..re-1 in chunks with the next chunk's energies loaded ahead. The single-map
+    // search (all fill warps, one CTA per SM) has registers to spare for 8-row chunks, whose
+    // compute covers an L2 round trip; kernels sized for several CTAs per SM keep 4-row chunks.
+    constexpr int CH = FWD ? 2 : ((CL && FWM >= FILL_WARPS_MAX) ? 8 : (CL ? 4 : 2));
     uint4 eb0[NP][CH], eb1[NP][CH];
     auto load_chunk = [&](uint4 (&eb)[NP][CH], int rbeg) {
 #pragma unroll
@@ -560,21 +562,38 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
       }
     }
     __syncwarp();
+    // lane 0 follows the directions up the window (relative columns, kept in the direction rows it
+    // has read: a row's entry is not needed again), then the warp writes the seam rows
+    uint32_t *path = reinterpret_cast<uint32_t *>(fd);   // fd[(i - rs) * 32] holds the column of row i
     if (lane == 0) {
-      int j = jbs;
+      int rel = jbs - x0;
+      bool okp = true;
       for (int i = re - 1; i >= first; --i) {
+        if (rel < 0 || rel >= FILL_W) { okp = false; break; }
+        const uint32_t dd = (fd[(i - rs) * 32 + (rel >> 3)] >> (2 * (rel & 7))) & 3u;
+        path[(i - rs) * 16] = (uint32_t)rel;   // the first 4 bytes of row i's direction words
+        rel += (int)dd - 1;
+      }
+      if (!okp) {
+        atomicOr(errw, ERR_FILL_MISMATCH);
+        rel = -1 - x0;
+      }
+      path[KS * 16 - 1] = (uint32_t)rel;    // the column above row `first` (row 0's seam when s == 0)
+      if (x0 + rel != jprev) atomicOr(errw, ERR_FILL_MISMATCH);
+    }
+    __syncwarp();
+    const bool path_ok = (int)path[KS * 16 - 1] + x0 >= 0;
+    if (path_ok) {
+      for (int i = first + lane; i < re; i += 32) {
+        const int j = x0 + (int)path[(i - rs) * 16];
         seam_out[i] = j;
         if (seam_log) seam_log[i] = j;
-        const int rel = j - x0;
-        if (rel < 0 || rel >= FILL_W) { atomicOr(errw, ERR_FILL_MISMATCH); j = -1; break; }
-        const uint32_t dd = (fd[(i - rs) * 32 + (rel >> 3)] >> (2 * (rel & 7))) & 3u;
-        j += (int)dd - 1;
       }
-      if (s == 0 && j >= 0) {
+      if (s == 0 && lane == 0) {
+        const int j = x0 + (int)path[KS * 16 - 1];
         seam_out[0] = j;
         if (seam_log) seam_log[0] = j;
       }
-      if (j != jprev) atomicOr(errw, ERR_FILL_MISMATCH);
     }
     __syncwarp();
   }
