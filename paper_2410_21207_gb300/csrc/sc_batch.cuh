@@ -78,7 +78,7 @@ __device__ void batch_seam_pass(const BatchItem &it, uint32_t *words, int rows, 
     __syncthreads();
     // energy rows compacted past the seam in place, the pair at the new columns s-1 and s; the
     // tails go through the rest of the idle ring, one buffer per warp
-    shift_rows_staged(Ecur, it.pe, rows, w, it.seam, pairs, warp, nwarps, lane, sbuf + (size_t)warp * sbuf_elems,
+    shift_rows_staged(Ecur, it.pe, rows, 0, 1, w, it.seam, pairs, warp, nwarps, lane, sbuf + (size_t)warp * sbuf_elems,
                       sbuf_elems);
     cur ^= 1;
     fence_proxy_async_global();   // the next search stages the compacted energy rows with TMA

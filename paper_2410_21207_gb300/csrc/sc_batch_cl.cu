@@ -31,7 +31,12 @@ __device__ void clb_seam_pass(const BatchItem &it, uint32_t *words, int rows, in
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   int16_t *lb[2] = {it.lists, it.lists + (size_t)rows * RPEND};
   // the staging ring is idle between searches: it holds the owned rows' refreshed pairs
-  uint32_t *pairs = reinterpret_cast<uint32_t *>(smem + search_plan<CLB_NW, CLB_KT, true, CLB_FILL_WARPS>(Smax).ring);
+  const SearchPlan plan = search_plan<CLB_NW, CLB_KT, true, CLB_FILL_WARPS>(Smax);
+  uint32_t *pairs = reinterpret_cast<uint32_t *>(smem + plan.ring);
+  const int nq = (rows - rank + cs - 1) / cs;   // rows this CTA owns
+  const size_t pair_bytes = ((size_t)(nq > 0 ? nq : 0) * 4 + 15) & ~(size_t)15;
+  uint16_t *sbuf = reinterpret_cast<uint16_t *>(smem + plan.ring + pair_bytes);
+  const int sbuf_elems = (int)(((plan.bars - plan.ring - pair_bytes) / nwarps) & ~(size_t)15) / 2;
   uint16_t *const Ecur = it.E + E_PADL;
   int cur = 0, m = 0;
   for (int t = 0; t < count; ++t) {
@@ -56,18 +61,9 @@ __device__ void clb_seam_pass(const BatchItem &it, uint32_t *words, int rows, in
     }
     if (bad) atomicOr(err, ERR_BAD_SEAM);
     cl.sync();
-    for (int q = warp; rank + q * cs < rows; q += nwarps) {
-      const int i = rank + q * cs;
-      const int s = it.seam[i];
-      if (s < 0 || s >= w) continue;
-      uint16_t *er = Ecur + (size_t)i * it.pe;
-      shift_row_u16(er, s, w, lane);
-      if (lane == 0) {
-        const uint32_t pr = pairs[q];
-        if (s >= 1) er[s - 1] = (uint16_t)(pr & 0xFFFFu);
-        if (s <= w - 2) er[s] = (uint16_t)(pr >> 16);
-      }
-    }
+    // the owned rows' energy tails, staged through the rest of the idle ring
+    shift_rows_staged(Ecur, it.pe, nq, rank, cs, w, it.seam, pairs, warp, nwarps, lane,
+                      sbuf + (size_t)warp * sbuf_elems, sbuf_elems);
     cur ^= 1;
     if (++m == RPEND) {
       for (int q = warp; rank + q * cs < rows; q += nwarps) {

@@ -203,31 +203,32 @@ __device__ __forceinline__ bool refresh_row(const uint32_t *img, int pitch, uint
   return true;
 }
 
-// The energy shift of every row this warp owns (rows warp, warp + nwarps, ...), each followed by
-// its refreshed pair (pairs[row]: e(s-1) | e(s) << 16). The tails of as many rows as fit the
+// The energy shift of every row this warp owns, each followed by its refreshed pair. The caller's
+// rows are numbered q = 0 .. nq-1 (image row row0 + q * rstride, refreshed pair pairs[q]:
+// e(s-1) | e(s) << 16); this warp owns q = warp, warp + nwarps, ... The tails of as many rows as fit the
 // warp's shared-memory buffer (buf_elems uint16, 16-byte aligned) are copied in with cp.async, all
 // in flight at once, then written back one element to the left; eight lanes work on each row, four
 // rows at a time, so no per-row chain of dependent steps is paid row after row. Rows whose seam is
 // out of range are skipped (the caller records the error).
-__device__ inline void shift_rows_staged(uint16_t *E, int pe, int rows, int w, const int32_t *seam,
-                                         const uint32_t *pairs, int warp, int nwarps, int lane, uint16_t *buf,
-                                         int buf_elems) {
+__device__ inline void shift_rows_staged(uint16_t *E, int pe, int nq, int row0, int rstride, int w,
+                                         const int32_t *seam, const uint32_t *pairs, int warp, int nwarps, int lane,
+                                         uint16_t *buf, int buf_elems) {
   const int sub = lane >> 3, sl = lane & 7;
   const int c_last = (w - 2) >> 3;   // the chunk holding the new last column
   // the warp's rows in blocks of 32: one seam load per lane, read back with shuffles
-  for (int blk = warp; blk < rows; blk += 32 * nwarps) {
-    const int my_row = blk + lane * nwarps;
-    const int my_s = my_row < rows ? seam[my_row] : -1;
-    const int nb = min(32, (rows - blk + nwarps - 1) / nwarps);
+  for (int blk = warp; blk < nq; blk += 32 * nwarps) {
+    const int my_q = blk + lane * nwarps;
+    const int my_s = my_q < nq ? seam[row0 + my_q * rstride] : -1;
+    const int nb = min(32, (nq - blk + nwarps - 1) / nwarps);
     int k = 0;
     while (k < nb) {
       // a group of rows whose tails fit the buffer; lane q records group row q (block index, offset)
       int info_k = 0, info_off = 0, ng = 0, used = 0;
       while (k < nb) {
-        const int i = blk + k * nwarps;
+        const int i = blk + k * nwarps;   // local row: image row row0 + i * rstride
         const int s = __shfl_sync(0xffffffffu, my_s, k);
         if (s < 0 || s >= w) { ++k; continue; }
-        uint16_t *er = E + (size_t)i * pe;
+        uint16_t *er = E + (size_t)(row0 + i * rstride) * pe;
         if (s >= w - 1) {   // nothing to shift: only the left refreshed value
           if (lane == 0 && s >= 1) er[s - 1] = (uint16_t)(pairs[i] & 0xFFFFu);
           ++k;
@@ -261,7 +262,7 @@ __device__ inline void shift_rows_staged(uint16_t *E, int pe, int rows, int w, c
         const int off = __shfl_sync(0xffffffffu, info_off, qq);
         const int s = __shfl_sync(0xffffffffu, my_s, kk);
         if (q < ng) {
-          const uint16_t *er = E + (size_t)(blk + kk * nwarps) * pe;
+          const uint16_t *er = E + (size_t)(row0 + (blk + kk * nwarps) * rstride) * pe;
           const int c_lo = s >> 3, nch = c_last - c_lo + 2;
           for (int c = sl; c < nch; c += 8) cp_async16(buf + off + 8 * c, er + 8 * (c_lo + c));
         }
@@ -276,7 +277,7 @@ __device__ inline void shift_rows_staged(uint16_t *E, int pe, int rows, int w, c
         const int s = __shfl_sync(0xffffffffu, my_s, kk);
         if (q < ng) {
           const int r = blk + kk * nwarps;
-          uint16_t *er = E + (size_t)r * pe;
+          uint16_t *er = E + (size_t)(row0 + r * rstride) * pe;
           const uint16_t *b = buf + off;
           const int c_lo = s >> 3;
           for (int c = c_lo + sl; c <= c_last; c += 8) {

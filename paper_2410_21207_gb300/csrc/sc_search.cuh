@@ -493,9 +493,10 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
 #pragma unroll
     for (int u = 0; u < 8; ++u) m[u] |= oob[u];
     // rows first..re-1 in chunks with the next chunk's energies loaded ahead. The single-map
-    // search (all fill warps, one CTA per SM) has registers to spare for 8-row chunks, whose
-    // compute covers an L2 round trip; kernels sized for several CTAs per SM keep 4-row chunks.
-    constexpr int CH = FWD ? 2 : ((CL && FWM >= FILL_WARPS_MAX) ? 8 : (CL ? 4 : 2));
+    // search (all fill warps, one CTA per SM, latency-bound) has registers to spare for 8-row
+    // chunks, whose compute covers an L2 round trip; the batched and multi-map kernels, whose
+    // latency other CTAs hide and whose registers are capped, use 2-row chunks.
+    constexpr int CH = FWD ? 2 : ((CL && FWM >= FILL_WARPS_MAX) ? 8 : 2);
     uint4 eb0[NP][CH], eb1[NP][CH];
     auto load_chunk = [&](uint4 (&eb)[NP][CH], int rbeg) {
 #pragma unroll
