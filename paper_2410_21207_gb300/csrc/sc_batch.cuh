@@ -84,15 +84,15 @@ __device__ void batch_seam_pass(const BatchItem &it, uint32_t *words, int rows, 
     fence_proxy_async_global();   // the next search stages the compacted energy rows with TMA
     __syncthreads();
     if (++m == RPEND) {
-      for (int i = warp; i < rows; i += nwarps)
-        compact_row_lazy(words + (size_t)i * it.pitch, lb[cur] + (size_t)i * RPEND, m, w - 1, lane);
+      compact_rows_staged(words, it.pitch, rows, 0, 1, lb[cur], m, w - 1, warp, nwarps, lane,
+                          reinterpret_cast<uint32_t *>(sbuf + (size_t)warp * sbuf_elems), sbuf_elems / 2);
       m = 0;
       __syncthreads();
     }
   }
   if (m > 0) {
-    for (int i = warp; i < rows; i += nwarps)
-      compact_row_lazy(words + (size_t)i * it.pitch, lb[cur] + (size_t)i * RPEND, m, cols - count, lane);
+    compact_rows_staged(words, it.pitch, rows, 0, 1, lb[cur], m, cols - count, warp, nwarps, lane,
+                        reinterpret_cast<uint32_t *>(sbuf + (size_t)warp * sbuf_elems), sbuf_elems / 2);
     __syncthreads();
   }
 }

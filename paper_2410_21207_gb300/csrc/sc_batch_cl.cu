@@ -66,20 +66,16 @@ __device__ void clb_seam_pass(const BatchItem &it, uint32_t *words, int rows, in
                       sbuf + (size_t)warp * sbuf_elems, sbuf_elems);
     cur ^= 1;
     if (++m == RPEND) {
-      for (int q = warp; rank + q * cs < rows; q += nwarps) {
-        const int i = rank + q * cs;
-        compact_row_lazy(words + (size_t)i * it.pitch, lb[cur] + (size_t)i * RPEND, m, w - 1, lane);
-      }
+      compact_rows_staged(words, it.pitch, nq, rank, cs, lb[cur], m, w - 1, warp, nwarps, lane,
+                          reinterpret_cast<uint32_t *>(sbuf + (size_t)warp * sbuf_elems), sbuf_elems / 2);
       m = 0;
     }
     fence_async_global();   // the next search stages the compacted energy rows with TMA
     cl.sync();
   }
   if (m > 0) {
-    for (int q = warp; rank + q * cs < rows; q += nwarps) {
-      const int i = rank + q * cs;
-      compact_row_lazy(words + (size_t)i * it.pitch, lb[cur] + (size_t)i * RPEND, m, cols - count, lane);
-    }
+    compact_rows_staged(words, it.pitch, nq, rank, cs, lb[cur], m, cols - count, warp, nwarps, lane,
+                        reinterpret_cast<uint32_t *>(sbuf + (size_t)warp * sbuf_elems), sbuf_elems / 2);
     cl.sync();
   }
 }

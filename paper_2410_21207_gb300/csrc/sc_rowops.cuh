@@ -313,6 +313,51 @@ __device__ inline void shift_rows_staged(uint16_t *E, int pe, int nq, int row0, 
   }
 }
 
+// compact_row_lazy for every row this warp owns (local rows q = warp, warp + nwarps, ... of nq;
+// image row row0 + q * rstride), staged through a shared-memory buffer of buf_words words
+// (16-byte aligned): the stored tail of a row is copied in with cp.async in pieces, then every
+// output word is gathered from the buffer. The removals are held one per lane (o_q - q in lane q);
+// for 32 consecutive outputs one ballot counts those left of the first and a second finds the few
+// that fall inside, instead of comparing every output with every removal.
+__device__ inline void compact_rows_staged(uint32_t *img, int pitch, int nq, int row0, int rstride,
+                                           const int16_t *lists, int m, int w, int warp, int nwarps, int lane,
+                                           uint32_t *buf, int buf_words) {
+  const int piece = ((buf_words - 24) / 32) * 32;   // outputs per staged piece
+  for (int q = warp; q < nq; q += nwarps) {
+    const int r = row0 + q * rstride;
+    uint32_t *row = img + (int64_t)r * pitch;
+    const int16_t *list = lists + (int64_t)r * RPEND;
+    if (piece < 32) {   // no room to stage: the direct form
+      compact_row_lazy(row, list, m, w, lane);
+      continue;
+    }
+    const int lq = lane < m ? (int)list[lane] - lane : 0x7FFFFFFF;
+    const int first = m > 0 ? __shfl_sync(0xffffffffu, lq, 0) : w;   // the list is sorted
+    for (int j0 = first; j0 < w; j0 += piece) {
+      const int j1 = min(w, j0 + piece);
+      const int a = j0 & ~3, b = (j1 + m + 3) & ~3;   // stored words j0 .. j1 + m - 1, 16-byte aligned
+      for (int x = a + 4 * lane; x < b; x += 128) cp_async16(buf + (x - a), row + x);
+      cp_async_wait_all();
+      __syncwarp();
+      for (int jb = j0; jb < j1; jb += 32) {
+        const int j = jb + lane;
+        int c = __popc(__ballot_sync(0xffffffffu, lq <= jb));
+        unsigned in = __ballot_sync(0xffffffffu, lq > jb && lq < jb + 32);
+        while (in) {
+          const int bq = __ffs(in) - 1;
+          in &= in - 1;
+          const int lv = __shfl_sync(0xffffffffu, lq, bq);
+          c += (j >= lv) ? 1 : 0;
+        }
+        const uint32_t v = (j < j1) ? buf[j + c - a] : 0u;
+        __syncwarp();
+        if (j < j1) row[j] = v;
+      }
+      __syncwarp();   // the buffer is reused by the next piece
+    }
+  }
+}
+
 // ---- forward energy ----
 // The three cost planes of pixel (i, j) of a rows x cols word image: CU = |P(i,j+1) - P(i,j-1)|
 // (0 at the first and last column), DL = |P(i-1,j) - P(i,j-1)| (0 in row 0 and column 0),
