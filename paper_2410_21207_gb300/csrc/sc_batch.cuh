@@ -11,6 +11,10 @@
 
 namespace sc {
 
+// Backtrack-fill warps of the one-CTA kernel: every warp of the CTA (one round of fills for images
+// up to 64 * (NW + 1) rows), except where that would overflow shared memory (15 warps, 16-row tiles).
+__host__ __device__ constexpr int batch_fill_warps(int nw, int kt) { return (nw == 15 && kt == 16) ? 8 : 16; }
+
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // rows x cols word image -> its transpose (cols x rows), 32x32 tiles staged in shared memory; `tile`
@@ -47,7 +51,7 @@ __device__ void batch_seam_pass(const BatchItem &it, uint32_t *words, int rows, 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   int16_t *lb[2] = {it.lists, it.lists + (size_t)rows * RPEND};
   // the staging ring is idle between searches: it holds the rows' refreshed pairs
-  const SearchPlan plan = search_plan<NW, KT, false>(Smax);
+  const SearchPlan plan = search_plan<NW, KT, false, batch_fill_warps(NW, KT)>(Smax);
   uint32_t *pairs = reinterpret_cast<uint32_t *>(smem + plan.ring);
   const size_t pair_bytes = ((size_t)rows * 4 + 15) & ~(size_t)15;
   uint16_t *sbuf = reinterpret_cast<uint16_t *>(smem + plan.ring + pair_bytes);
@@ -67,7 +71,7 @@ __device__ void batch_seam_pass(const BatchItem &it, uint32_t *words, int rows, 
     a.cost = costs ? costs + t : nullptr;
     a.err = err;
     a.gated = false;
-    seam_search<NW, KT, false>(a, smem, Smax, st);   // ends with a CTA barrier: the seam is complete
+    seam_search<NW, KT, false, batch_fill_warps(NW, KT)>(a, smem, Smax, st);   // ends with a CTA barrier: the seam is complete
     // every row's refreshed pair and list update, one thread per row (into the idle staging ring)
     bool bad = false;
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
@@ -122,7 +126,7 @@ __device__ void batch_carve_item(const BatchItem &it, unsigned char *smem, int S
   batch_seam_pass<NW, KT>(it, it.img_w, H, W, nv, it.seam_log, it.cost_log, smem, Smax, st, err);
   uint32_t *res = it.img_w;
   if (nh > 0) {
-    const SearchPlan plan = search_plan<NW, KT, false>(Smax);
+    const SearchPlan plan = search_plan<NW, KT, false, batch_fill_warps(NW, KT)>(Smax);
     uint32_t *tile = reinterpret_cast<uint32_t *>(smem + plan.ring);   // the ring is idle between searches
     const int ntw_fit = (int)((plan.bars - plan.ring) / (32 * 33 * 4));
     const int ntw = ntw_fit < NW + 1 ? ntw_fit : NW + 1;
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(Geo<NW, KT, false>::THREADS, 1)
   // the current image's descriptor lives in shared memory and its fields are read where they are
   // used, so they do not occupy registers across the seam loop
   __shared__ BatchItem cur;
-  search_init<NW, KT, false>(smem, Smax);
+  search_init<NW, KT, false, batch_fill_warps(NW, KT)>(smem, Smax);
   __syncthreads();
   SearchState st;
   for (;;) {
@@ -185,7 +189,7 @@ cudaError_t batch_configure_cfg() {
 template <int NW, int KT>
 cudaError_t launch_batch_cfg(const BatchItem *items, int n, int Smax, int grid, int *queue, int *err,
                              cudaStream_t st) {
-  const size_t smem = search_plan<NW, KT, false>(Smax).total;
+  const size_t smem = search_plan<NW, KT, false, batch_fill_warps(NW, KT)>(Smax).total;
   if (smem > BATCH_SMEM_MAX) return cudaErrorInvalidValue;
   cudaError_t e = batch_configure_cfg<NW, KT>();
   if (e != cudaSuccess) return e;

@@ -6,7 +6,7 @@
 namespace sc {
 
 #define SC_BATCH_CASES(X) X(12, 8) X(12, 16)
-#define SC_SMEM(N, K) case K: return search_plan<N, K, false>(Smax).total;
+#define SC_SMEM(N, K) case K: return search_plan<N, K, false, batch_fill_warps(N, K)>(Smax).total;
 #define SC_OCC(N, K) case K: batch_configure_cfg<N, K>(); \
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<N, K>, Geo<N, K, false>::THREADS, smem); break;
 #define SC_LAUNCH(N, K) case K: return launch_batch_cfg<N, K>(items, n, Smax, grid, queue, err, st);
