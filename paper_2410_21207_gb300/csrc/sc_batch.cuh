@@ -12,8 +12,8 @@
 namespace sc {
 
 // Backtrack-fill warps of the one-CTA kernel: every warp of the CTA (one round of fills for images
-// up to 64 * (NW + 1) rows), except where that would overflow shared memory (15 warps, 16-row tiles).
-__host__ __device__ constexpr int batch_fill_warps(int nw, int kt) { return (nw == 15 && kt == 16) ? 8 : 16; }
+// up to 64 * (NW + 1) rows); their direction rows share the idle staging ring.
+__host__ __device__ constexpr int batch_fill_warps(int nw, int kt) { return 16; }
 
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 

@@ -79,8 +79,12 @@ __host__ __device__ inline SearchPlan search_plan(int S) {
   p.cmin = o; o += 8;
   p.jb = o;   o += (size_t)(S + 1) * 4;  o = (o + 15) & ~(size_t)15;
   p.misc = o; o += 16;
-  p.fdir = o; o += (size_t)G::FW * KS * 32 * 2;  o = (o + 15) & ~(size_t)15;
-  p.ring = o; o += (size_t)NSLOT * (FWD ? 3 : 1) * KT * G::BW * 2;  o = (o + 15) & ~(size_t)15;
+  // the backtrack fill's direction rows live in the staging ring, which is idle by then (every
+  // staged tile has been consumed before the argmin), unless the ring is the smaller of the two
+  const size_t fdir_sz = (size_t)G::FW * KS * 32 * 2, ring_sz = (size_t)NSLOT * (FWD ? 3 : 1) * KT * G::BW * 2;
+  if (fdir_sz > ring_sz) { p.fdir = o; o += fdir_sz;  o = (o + 15) & ~(size_t)15; }
+  p.ring = o; o += ring_sz;  o = (o + 15) & ~(size_t)15;
+  if (fdir_sz <= ring_sz) p.fdir = p.ring;
   p.bars = o; o += (size_t)(2 * NSLOT + 2) * 8;   // full[NSLOT], empty[NSLOT], halo[2]
   p.total = (o + 15) & ~(size_t)15;
   return p;
@@ -376,7 +380,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
           // columns come from the neighbours instead
           if (strip_lane && (!exch || (c0 >= A && c0 < B)))
             *reinterpret_cast<uint4 *>(bnd + (t & 1) * BW + bidx0) = v;
-          if (CL && exch) {
+          if constexpr (CL) if (exch) {
             const uint32_t xg = st.exch + (uint32_t)((r0 + KT) / K2 - 1);
             const int par = (int)(xg & 1);
             // my first K2 own columns are the left neighbour's right halo, my last K2 the right's left
