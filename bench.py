@@ -57,6 +57,20 @@ def _dist():
     return ws, rank, local
 
 
+def replica_throughput(local_s: float, units: int, ws: int, device):
+    """Whole-job throughput of ws independent replicas (one per rank, each doing `units` units in
+    `local_s` seconds): the units of all ranks over the slowest rank's time (a MAX all-reduce over
+    the process group when ws > 1). Returns (units per second, max seconds)."""
+    total_s = local_s
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([local_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    return units * ws / total_s, total_s
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -579,13 +593,7 @@ def run_native(a):
     dp_ms, dp_n = sc.timing_read("dp")
     _, launches = sc.timing_read("all")
     launches //= max(1, a.steps)
-    total_s = sum(step_ms) / 1000.0
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = seams * a.steps * ws / total_s
+    value, total_s = replica_throughput(sum(step_ms) / 1000.0, seams * a.steps, ws, dev)
 
     # roofline of the dominant kernel (the DP seam search): algorithmic bytes = H*W_cur*2.25 per launch
     dp_bytes = 2.25 * sum(H * (W - t) for t in range(W - tw)) + 2.25 * sum(tw * (H - t) for t in range(H - th))
