@@ -26,9 +26,9 @@
 //   * Energies are staged in shared memory by TMA: a producer warp issues one bulk copy per row
 //     (one row per lane) into an NSLOT-slot ring, gated by full/empty mbarriers; a lane reads its 4
 //     energies of a row with one 8-byte shared-memory load.
-//   * The rows of a full tile are branch-free; row 0 and a ragged last tile take a general path,
-//     and per-super-tile bookkeeping runs after the tile, on its last row (the only row of a full
-//     tile where it can occur, since KS is a multiple of KT).
+//   * The rows of a tile are branch-free (row 0 initialises from its energies; a ragged last tile
+//     runs a counted loop), and per-super-tile bookkeeping runs after the tile, on its last row
+//     (the only row of a tile where it can occur, since KS is a multiple of KT).
 // The result is Algorithm 3's seam exactly (leftmost ties, leftmost last-row minimum).
 // With FWD (forward energy) the map has three planes, CU, DL and DR, and a cell's cost depends on
 // the direction it is reached from: M(i,j) = CU(i,j) + min(M(i-1,j-1) + DL(i,j), M(i-1,j),
@@ -49,6 +49,7 @@ constexpr uint32_t SENT = 0xFFFFFFFFu;   // excluded (outside the image): above 
 constexpr int FILL_W = 256;              // backtrack-fill window (8 columns per lane)
 constexpr int FILL_WARPS_MAX = 8;        // warps that run backtrack fills
 constexpr int NSLOT = 3;                 // energy staging ring: tiles in flight
+constexpr size_t SEARCH_SMEM_LIMIT = 232448;   // opt-in dynamic shared memory per CTA
 
 template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX>
 struct Geo {
@@ -64,7 +65,8 @@ struct Geo {
 
 // offsets of the dynamic shared-memory regions used by seam_search
 struct SearchPlan {
-  size_t bnd, hbuf, anc, wmin, cmin, jb, misc, fdir, ring, bars, total;
+  size_t bnd, hbuf, anc, wmin, cmin, jb, misc, fdir, ring, bars, gat, total;
+  int gw;   // row stride (bytes) of the gathered ancestor table in rank 0; 0: not gathered
 };
 
 template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false>
@@ -76,7 +78,7 @@ __host__ __device__ inline SearchPlan search_plan(int S) {
   p.hbuf = o; o += CL ? (size_t)2 * 2 * K2 * 4 : 0;
   p.anc = o;  o += (size_t)S * G::OWC;  o = (o + 15) & ~(size_t)15;
   p.wmin = o; o += (size_t)(NW + 1) * 8;
-  p.cmin = o; o += 8;
+  p.cmin = o; o += CL ? (size_t)MAX_CLUSTER * 8 : 8;   // every CTA's minimum, pushed to rank 0
   p.jb = o;   o += (size_t)(S + 1) * 4;  o = (o + 15) & ~(size_t)15;
   p.misc = o; o += 16;
   // the backtrack fill's direction rows live in the staging ring, which is idle by then (every
@@ -86,6 +88,17 @@ __host__ __device__ inline SearchPlan search_plan(int S) {
   p.ring = o; o += ring_sz;  o = (o + 15) & ~(size_t)15;
   if (fdir_sz <= ring_sz) p.fdir = p.ring;
   p.bars = o; o += (size_t)(2 * NSLOT + 2) * 8;   // full[NSLOT], empty[NSLOT], halo[2]
+  o = (o + 15) & ~(size_t)15;
+  // single-map cluster search: every CTA writes its super-tile ancestors straight into rank 0's
+  // table (remote stores during the row loop), so the chain after the argmin is all local loads;
+  // only where the table fits
+  p.gat = o;
+  p.gw = 0;
+  const size_t gat_sz = (size_t)S * MAX_CLUSTER * G::OWC;
+  if (CL && FWM >= FILL_WARPS_MAX && o + gat_sz <= SEARCH_SMEM_LIMIT) {
+    p.gw = MAX_CLUSTER * G::OWC;
+    o += gat_sz;
+  }
   p.total = (o + 15) & ~(size_t)15;
   return p;
 }
@@ -116,18 +129,21 @@ __device__ __forceinline__ uint32_t lo8(uint32_t x) { return __byte_perm(x, 0u, 
 __device__ __forceinline__ uint32_t hi8(uint32_t x) { return __byte_perm(x, 0u, 0x4324); }
 
 // Bookkeeping after row i (keys k of this lane's V columns, warp frame base fb):
-//  - bottom of a super-tile: record the ancestors of the CTA-own columns (one byte: a - col + 128);
+//  - bottom of a super-tile: record the ancestors of the CTA-own columns (one byte: a - col + 128),
+//    in rank 0's gathered table (row stride gw) when there is one, else in this CTA's table;
 //  - last row before a super-tile: save the raw cost row for the backtrack fill;
 //  - last row of the image: fold the lane's (M << 32 | column) minimum.
 __device__ __forceinline__ void row_events(int i, const uint32_t (&k)[V], int H, int W, int c0, int fb, bool cta_own,
                                            int A, uint32_t *__restrict__ Mrow, int pitch_e,
-                                           uint8_t *__restrict__ ancT, int OWC, unsigned long long &lastmin) {
+                                           uint8_t *__restrict__ ancT, int OWC, uint8_t *gat, int gw,
+                                           unsigned long long &lastmin) {
   if (!cta_own) return;
   if (((i + 1) % KS == 0) || (i == H - 1)) {
     const uint32_t d = (uint32_t)(fb - c0 + 128);
     const uint32_t a = ((k[0] + d) & 0xFFu) | (((k[1] + d - 1u) & 0xFFu) << 8) | (((k[2] + d - 2u) & 0xFFu) << 16) |
                        (((k[3] + d - 3u) & 0xFFu) << 24);
-    *reinterpret_cast<uint32_t *>(ancT + (size_t)(i / KS) * OWC + (c0 - A)) = a;
+    if (gw) *reinterpret_cast<uint32_t *>(gat + (size_t)(i / KS) * gw + c0) = a;
+    else *reinterpret_cast<uint32_t *>(ancT + (size_t)(i / KS) * OWC + (c0 - A)) = a;
   }
   if (((i + 1) % KS == 0) && (i + 1 < H)) {
     uint4 m;
@@ -145,22 +161,31 @@ __device__ __forceinline__ void row_events(int i, const uint32_t (&k)[V], int H,
   }
 }
 
+// key + energy, forced to SENT where the mask is SENT (outside the image). max(x + e, mask) equals
+// (x + e) | mask for a mask of 0 or SENT, and the fused add-max keeps the mask off the row chain's
+// critical path better than a separate OR.
+template <bool MASK>
+__device__ __forceinline__ uint32_t add_mask(uint32_t x, uint32_t e, uint32_t mask) {
+  if (MASK) return __viaddmax_u32(x, e, mask);
+  return x + e;
+}
+
 // One DP row for a lane: keys k (previous row) -> next row; energies ev (4 x uint16).
+template <bool MASK>
 __device__ __forceinline__ void dp_row(uint32_t (&k)[V], uint2 ev, const uint32_t (&oobm)[V]) {
   const uint32_t e0 = lo8(ev.x), e1 = hi8(ev.x), e2 = lo8(ev.y), e3 = hi8(ev.y);
   const uint32_t L = __shfl_up_sync(0xffffffffu, k[V - 1], 1);
   const uint32_t R = __shfl_down_sync(0xffffffffu, k[0], 1);
-  const uint32_t n0 = (min3u(L, k[0], k[1]) + e0) | oobm[0];
-  const uint32_t n1 = (min3u(k[0], k[1], k[2]) + e1) | oobm[1];
-  const uint32_t n2 = (min3u(k[1], k[2], k[3]) + e2) | oobm[2];
-  const uint32_t n3 = (min3u(k[2], k[3], R) + e3) | oobm[3];
+  const uint32_t n0 = add_mask<MASK>(min3u(L, k[0], k[1]), e0, oobm[0]);
+  const uint32_t n1 = add_mask<MASK>(min3u(k[0], k[1], k[2]), e1, oobm[1]);
+  const uint32_t n2 = add_mask<MASK>(min3u(k[1], k[2], k[3]), e2, oobm[2]);
+  const uint32_t n3 = add_mask<MASK>(min3u(k[2], k[3], R), e3, oobm[3]);
   k[0] = n0; k[1] = n1; k[2] = n2; k[3] = n3;
 }
 
 // KT rows of a full tile from the staged energies er (row stride BW); MASK applies oobm.
 template <int KT, int BW, bool MASK>
 __device__ __forceinline__ void dp_rows(uint32_t (&k)[V], const uint16_t *er, const uint32_t (&oobm)[V]) {
-  constexpr uint32_t Z[V] = {0u, 0u, 0u, 0u};
   uint2 a = *reinterpret_cast<const uint2 *>(er);
   uint2 b = *reinterpret_cast<const uint2 *>(er + BW);
 #pragma unroll
@@ -168,25 +193,42 @@ __device__ __forceinline__ void dp_rows(uint32_t (&k)[V], const uint16_t *er, co
     const uint2 ev = a;
     a = b;
     if (r + 2 < KT) b = *reinterpret_cast<const uint2 *>(er + (r + 2) * BW);
-    dp_row(k, ev, MASK ? oobm : Z);
+    dp_row<MASK>(k, ev, oobm);
+  }
+}
+
+// Rows rb .. n-1 (n <= KT) of a tile: the first tile (rb = 1, row 0 initialises) or a ragged
+// last tile, at the pace of a full tile.
+template <int KT, int BW, bool MASK>
+__device__ __forceinline__ void dp_rows_n(uint32_t (&k)[V], const uint16_t *er, const uint32_t (&oobm)[V], int rb,
+                                          int n) {
+  uint2 a = *reinterpret_cast<const uint2 *>(er + rb * BW);
+  uint2 b = a;
+  if (rb + 1 < n) b = *reinterpret_cast<const uint2 *>(er + (rb + 1) * BW);
+#pragma unroll 2
+  for (int r = rb; r < n; ++r) {
+    const uint2 ev = a;
+    a = b;
+    if (r + 2 < n) b = *reinterpret_cast<const uint2 *>(er + (r + 2) * BW);
+    dp_row<MASK>(k, ev, oobm);
   }
 }
 
 // One forward-energy row: keys k (previous row) -> next row; cu, dl, dr: 4 x uint16 each.
+template <bool MASK>
 __device__ __forceinline__ void dp_row_fwd(uint32_t (&k)[V], uint2 cu, uint2 dl, uint2 dr, const uint32_t (&oobm)[V]) {
   const uint32_t L = __shfl_up_sync(0xffffffffu, k[V - 1], 1);
   const uint32_t R = __shfl_down_sync(0xffffffffu, k[0], 1);
-  const uint32_t n0 = (min3u(L + lo8(dl.x), k[0], k[1] + lo8(dr.x)) + lo8(cu.x)) | oobm[0];
-  const uint32_t n1 = (min3u(k[0] + hi8(dl.x), k[1], k[2] + hi8(dr.x)) + hi8(cu.x)) | oobm[1];
-  const uint32_t n2 = (min3u(k[1] + lo8(dl.y), k[2], k[3] + lo8(dr.y)) + lo8(cu.y)) | oobm[2];
-  const uint32_t n3 = (min3u(k[2] + hi8(dl.y), k[3], R + hi8(dr.y)) + hi8(cu.y)) | oobm[3];
+  const uint32_t n0 = add_mask<MASK>(min3u(L + lo8(dl.x), k[0], k[1] + lo8(dr.x)), lo8(cu.x), oobm[0]);
+  const uint32_t n1 = add_mask<MASK>(min3u(k[0] + hi8(dl.x), k[1], k[2] + hi8(dr.x)), hi8(cu.x), oobm[1]);
+  const uint32_t n2 = add_mask<MASK>(min3u(k[1] + lo8(dl.y), k[2], k[3] + lo8(dr.y)), lo8(cu.y), oobm[2]);
+  const uint32_t n3 = add_mask<MASK>(min3u(k[2] + hi8(dl.y), k[3], R + hi8(dr.y)), hi8(cu.y), oobm[3]);
   k[0] = n0; k[1] = n1; k[2] = n2; k[3] = n3;
 }
 
 // KT forward-energy rows of a full tile; the three planes are KT rows apart in the staging ring.
 template <int KT, int BW, bool MASK>
 __device__ __forceinline__ void dp_rows_fwd(uint32_t (&k)[V], const uint16_t *er, const uint32_t (&oobm)[V]) {
-  constexpr uint32_t Z[V] = {0u, 0u, 0u, 0u};
   constexpr int PL = KT * BW;
   uint2 a0 = *reinterpret_cast<const uint2 *>(er), a1 = *reinterpret_cast<const uint2 *>(er + PL),
         a2 = *reinterpret_cast<const uint2 *>(er + 2 * PL);
@@ -198,8 +240,19 @@ __device__ __forceinline__ void dp_rows_fwd(uint32_t (&k)[V], const uint16_t *er
       a1 = *reinterpret_cast<const uint2 *>(er + PL + (r + 1) * BW);
       a2 = *reinterpret_cast<const uint2 *>(er + 2 * PL + (r + 1) * BW);
     }
-    dp_row_fwd(k, c0, c1, c2, MASK ? oobm : Z);
+    dp_row_fwd<MASK>(k, c0, c1, c2, oobm);
   }
+}
+
+// Forward-energy rows rb .. n-1 (n <= KT) of a first or ragged last tile.
+template <int KT, int BW, bool MASK>
+__device__ __forceinline__ void dp_rows_n_fwd(uint32_t (&k)[V], const uint16_t *er, const uint32_t (&oobm)[V], int rb,
+                                              int n) {
+  constexpr int PL = KT * BW;
+  for (int r = rb; r < n; ++r)
+    dp_row_fwd<MASK>(k, *reinterpret_cast<const uint2 *>(er + r * BW),
+                     *reinterpret_cast<const uint2 *>(er + PL + r * BW),
+                     *reinterpret_cast<const uint2 *>(er + 2 * PL + r * BW), oobm);
 }
 
 // Initialise the staging and halo mbarriers (thread 0; the caller then synchronises the CTA, and
@@ -252,6 +305,9 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + plan.bars);
   uint64_t *empty = full + NSLOT;
   uint64_t *hbar = empty + NSLOT;
+  const int gw = plan.gw;
+  uint8_t *const gat = smem + plan.gat;
+  uint8_t *const gat0 = (CL && gw) ? cg::this_cluster().map_shared_rank(gat, 0) : gat;
 
   // geometry
   const int A = rank * OWC, B = A + OWC;
@@ -348,28 +404,26 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[slot]);   // this warp is done with the staged rows
           if (((r0 + KT) % KS) == 0 || r0 + KT == H)
-            row_events(r0 + KT - 1, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, lastmin);
+            row_events(r0 + KT - 1, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, gat0, gw, lastmin);
         } else {
-          // first tile (row 0 has no predecessor) or a ragged last tile
-          for (int r = 0; r < KT; ++r) {
-            const int i = r0 + r;
-            if (i >= H) break;
-            const uint2 ev = *reinterpret_cast<const uint2 *>(er + r * BW);   // CU with FWD
-            if (i == 0) {
-              k[0] = (lo8(ev.x) | own_a) | oobm[0];
-              k[1] = (hi8(ev.x) | (own_a + 1u)) | oobm[1];
-              k[2] = (lo8(ev.y) | (own_a + 2u)) | oobm[2];
-              k[3] = (hi8(ev.y) | (own_a + 3u)) | oobm[3];
-            } else if (FWD) {
-              dp_row_fwd(k, ev, *reinterpret_cast<const uint2 *>(er + KT * BW + r * BW),
-                         *reinterpret_cast<const uint2 *>(er + 2 * KT * BW + r * BW), oobm);
-            } else {
-              dp_row(k, ev, oobm);
-            }
-            row_events(i, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, lastmin);
+          // first tile (row 0 has no predecessor) or a ragged last tile. Neither holds a row with
+          // bookkeeping except the image's last row: a super-tile ends on a multiple of KS (a
+          // multiple of KT), which is never inside these tiles' rows 0 .. n-1 (n < KT for the
+          // ragged tile; the first tile ends at row KT-1 < KS-1)
+          const int n = (H - r0 < KT) ? H - r0 : KT;
+          if (t == 0) {
+            const uint2 ev = *reinterpret_cast<const uint2 *>(er);   // CU with FWD
+            k[0] = (lo8(ev.x) | own_a) | oobm[0];
+            k[1] = (hi8(ev.x) | (own_a + 1u)) | oobm[1];
+            k[2] = (lo8(ev.y) | (own_a + 2u)) | oobm[2];
+            k[3] = (hi8(ev.y) | (own_a + 3u)) | oobm[3];
           }
+          if (FWD) dp_rows_n_fwd<KT, BW, EDGE>(k, er, oobm, t == 0 ? 1 : 0, n);
+          else dp_rows_n<KT, BW, EDGE>(k, er, oobm, t == 0 ? 1 : 0, n);
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[slot]);
+          if (((r0 + n) % KS) == 0 || r0 + n == H)
+            row_events(r0 + n - 1, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, gat0, gw, lastmin);
         }
         if (more) {
           const bool exch = CL && ((r0 + KT) % K2 == 0) && cs > 1;
@@ -423,7 +477,8 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   if (threadIdx.x == 0) {
     unsigned long long m = ~0ull;
     for (int w = 0; w <= NW; ++w) m = wmin[w] < m ? wmin[w] : m;
-    *cmin = m;
+    if (CL) cg::this_cluster().map_shared_rank(cmin, 0)[rank] = m;   // pushed to rank 0
+    else cmin[0] = m;
   }
   group_sync<CL>();
 
@@ -431,13 +486,15 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   if (rank == 0 && threadIdx.x == 0) {
     int ok = !p.gated;
     unsigned long long best = ~0ull;
-    for (int r = 0; r < cs; ++r) {
-      const unsigned long long *rm = CL ? cg::this_cluster().map_shared_rank(cmin, r) : cmin;
-      best = *rm < best ? *rm : best;
-    }
+    for (int r = 0; r < cs; ++r) best = cmin[r] < best ? cmin[r] : best;
     int j = (int)(best & 0xFFFFFFFFull);
     if (ok && (j < 0 || j >= W)) { ok = 0; atomicOr(p.err, ERR_BAD_SEAM); }
-    for (int s = S - 1; ok && s >= 0; --s) {
+    for (int s = S - 1; ok && gw && s >= 0; --s) {
+      jb[s] = j;
+      j = j + (int)gat[(size_t)s * gw + j] - 128;
+      if (j < 0 || j >= W) { ok = 0; atomicOr(p.err, ERR_BAD_SEAM); }
+    }
+    for (int s = S - 1; ok && !gw && s >= 0; --s) {
       jb[s] = j;
       const int c = j / OWC;
       if (c < 0 || c >= cs) { ok = 0; atomicOr(p.err, ERR_BAD_SEAM); break; }
@@ -538,7 +595,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
           const uint32_t mn = min3u(a, b, c);
           const uint32_t dd = (a == mn) ? 0u : ((b == mn) ? 1u : 2u);
           dirs |= dd << (2 * u);
-          nm[u] = (mn + ee[u]) | oob[u];
+          nm[u] = add_mask<true>(mn, ee[u], oob[u]);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) m[u] = nm[u];
