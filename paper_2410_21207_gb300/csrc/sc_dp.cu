@@ -27,11 +27,18 @@ DpShape dp_shape_for(int W) {
   return s;
 }
 
+// Super-tile height: 32 rows for the 4-warp shape, whose every CTA has an SM to itself and whose
+// backtrack fill (KSS rows, serial) then halves; 64 rows for the wide shapes, whose ancestor chain
+// crosses CTAs (one DSMEM load per super-tile) and would double.
+template <int NW, int KT, bool FWD>
+__host__ __device__ constexpr int dp_super_rows() { return (NW == 4 && KT == 32 && !FWD) ? KS_MIN : KS; }
+
 template <int NW, int KT, bool FWD = false>
 __global__ void __launch_bounds__(Geo<NW, KT, true>::THREADS, 1) k_dp(DpArgs p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int S = (p.H + KS - 1) / KS;
-  search_init<NW, KT, true, FILL_WARPS_MAX, FWD>(smem, S);
+  constexpr int KSS = dp_super_rows<NW, KT, FWD>();
+  const int S = (p.H + KSS - 1) / KSS;
+  search_init<NW, KT, true, FILL_WARPS_MAX, FWD, KSS>(smem, S);
   // neighbours push into each other's halo buffers: every CTA's barriers must be initialised first
   cg::this_cluster().sync();
   // the set-up above overlaps the previous kernel of the seam loop; its results are read below
@@ -50,12 +57,13 @@ __global__ void __launch_bounds__(Geo<NW, KT, true>::THREADS, 1) k_dp(DpArgs p) 
   a.gated = (p.gate != nullptr) && (*p.gate & ERR_ENERGY_RANGE);
   a.pstride = p.pstride;
   SearchState st;
-  seam_search<NW, KT, true, FILL_WARPS_MAX, FWD>(a, smem, S, st);
+  seam_search<NW, KT, true, FILL_WARPS_MAX, FWD, KSS>(a, smem, S, st);
 }
 
 template <int NW, int KT, bool FWD = false>
 static cudaError_t launch_dp_shape(const DpArgs &a, int cs, cudaStream_t st) {
-  const size_t smem = search_plan<NW, KT, true, FILL_WARPS_MAX, FWD>((a.H + KS - 1) / KS).total;
+  constexpr int KSS = dp_super_rows<NW, KT, FWD>();
+  const size_t smem = search_plan<NW, KT, true, FILL_WARPS_MAX, FWD, KSS>((a.H + KSS - 1) / KSS).total;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_dp<NW, KT, FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);

@@ -14,21 +14,23 @@
 //     columns on either side of its own range and every K2 rows pushes its edge columns into the
 //     neighbours' shared memory with st.async; there is no cluster-wide barrier in the row loop.
 //   * A cost travels with an ancestor: key = (M << 8) | a, with a the column (in the warp's frame)
-//     where the cell's optimal path crossed the top of the current super-tile of KS rows. The
+//     where the cell's optimal path crossed the top of the current super-tile of KSS rows (64, or
+//     32 for the latency-bound single-map search, whose backtrack fill then halves). The
 //     unsigned minimum of three keys is the minimum M and, among equal M, the smallest ancestor.
 //     Optimal predecessors never cross under the leftmost tie-break (pred(j) <= pred(j+1): if
 //     pred(j) = j+1 then M(j+1) < M(j), so j+1 cannot pick j), hence ancestors are non-decreasing
 //     in the column and the smallest ancestor among tied candidates is the leftmost candidate's:
 //     the key minimum carries exactly Algorithm 3's choice. The bottom row of each super-tile
-//     records its ancestors; a chain of ceil(H/KS) lookups gives the seam column at every
+//     records its ancestors; a chain of ceil(H/KSS) lookups gives the seam column at every
 //     super-tile boundary, and then the super-tiles are backtracked in parallel by recomputing
-//     their KS rows in a 256-column window from a saved cost row with explicit directions.
+//     their KSS rows in a 4*KSS-column window (KSS/8 columns per lane) from a saved cost row with
+//     explicit directions.
 //   * Energies are staged in shared memory by TMA: a producer warp issues one bulk copy per row
 //     (one row per lane) into an NSLOT-slot ring, gated by full/empty mbarriers; a lane reads its 4
 //     energies of a row with one 8-byte shared-memory load.
 //   * The rows of a tile are branch-free (row 0 initialises from its energies; a ragged last tile
 //     runs a counted loop), and per-super-tile bookkeeping runs after the tile, on its last row
-//     (the only row of a tile where it can occur, since KS is a multiple of KT).
+//     (the only row of a tile where it can occur, since KSS is a multiple of KT).
 // The result is Algorithm 3's seam exactly (leftmost ties, leftmost last-row minimum).
 // With FWD (forward energy) the map has three planes, CU, DL and DR, and a cell's cost depends on
 // the direction it is reached from: M(i,j) = CU(i,j) + min(M(i-1,j-1) + DL(i,j), M(i-1,j),
@@ -46,12 +48,11 @@ namespace sc {
 namespace cg = cooperative_groups;
 
 constexpr uint32_t SENT = 0xFFFFFFFFu;   // excluded (outside the image): above every key
-constexpr int FILL_W = 256;              // backtrack-fill window (8 columns per lane)
 constexpr int FILL_WARPS_MAX = 8;        // warps that run backtrack fills
 constexpr int NSLOT = 3;                 // energy staging ring: tiles in flight
 constexpr size_t SEARCH_SMEM_LIMIT = 232448;   // opt-in dynamic shared memory per CTA
 
-template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX>
+template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, int KSS = KS>
 struct Geo {
   static constexpr int Q = 32 * V - 2 * KT;              // warp strip
   static constexpr int K2E = CL ? K2 : 0;                // CTA-level halo (clusters only)
@@ -59,8 +60,11 @@ struct Geo {
   static constexpr int OWC = NW * Q - 2 * K2E;           // CTA-own columns
   static constexpr int FW = (NW + 1) < FWM ? (NW + 1) : FWM;   // backtrack-fill warps
   static constexpr int THREADS = (NW + 1) * 32;          // compute warps + the producer warp
-  static_assert(Q > 0 && KS % KT == 0 && K2 % KT == 0, "tile geometry");
-  static_assert(Q + 2 * KS <= 256, "the ancestor frame must fit 8 bits");
+  static constexpr int FV = KSS / 8;                     // backtrack-fill columns per lane
+  static constexpr int FILLW = 32 * FV;                  // backtrack-fill window (4 * KSS columns)
+  static_assert(Q > 0 && KSS % KT == 0 && K2 % KT == 0, "tile geometry");
+  static_assert(KSS == 32 || KSS == 64, "super-tile height");
+  static_assert(Q + 2 * KSS <= 256, "the ancestor frame must fit 8 bits");
 };
 
 // offsets of the dynamic shared-memory regions used by seam_search
@@ -69,9 +73,9 @@ struct SearchPlan {
   int gw;   // row stride (bytes) of the gathered ancestor table in rank 0; 0: not gathered
 };
 
-template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false>
+template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false, int KSS = KS>
 __host__ __device__ inline SearchPlan search_plan(int S) {
-  using G = Geo<NW, KT, CL, FWM>;
+  using G = Geo<NW, KT, CL, FWM, KSS>;
   SearchPlan p;
   size_t o = 0;
   p.bnd = o;  o += (size_t)2 * G::BW * 4;  o = (o + 15) & ~(size_t)15;
@@ -83,7 +87,7 @@ __host__ __device__ inline SearchPlan search_plan(int S) {
   p.misc = o; o += 16;
   // the backtrack fill's direction rows live in the staging ring, which is idle by then (every
   // staged tile has been consumed before the argmin), unless the ring is the smaller of the two
-  const size_t fdir_sz = (size_t)G::FW * KS * 32 * 2, ring_sz = (size_t)NSLOT * (FWD ? 3 : 1) * KT * G::BW * 2;
+  const size_t fdir_sz = (size_t)G::FW * KSS * 32 * (G::FV == 4 ? 4 : 2), ring_sz = (size_t)NSLOT * (FWD ? 3 : 1) * KT * G::BW * 2;
   if (fdir_sz > ring_sz) { p.fdir = o; o += fdir_sz;  o = (o + 15) & ~(size_t)15; }
   p.ring = o; o += ring_sz;  o = (o + 15) & ~(size_t)15;
   if (fdir_sz <= ring_sz) p.fdir = p.ring;
@@ -133,22 +137,23 @@ __device__ __forceinline__ uint32_t hi8(uint32_t x) { return __byte_perm(x, 0u, 
 //    in rank 0's gathered table (row stride gw) when there is one, else in this CTA's table;
 //  - last row before a super-tile: save the raw cost row for the backtrack fill;
 //  - last row of the image: fold the lane's (M << 32 | column) minimum.
+template <int KSS>
 __device__ __forceinline__ void row_events(int i, const uint32_t (&k)[V], int H, int W, int c0, int fb, bool cta_own,
                                            int A, uint32_t *__restrict__ Mrow, int pitch_e,
                                            uint8_t *__restrict__ ancT, int OWC, uint8_t *gat, int gw,
                                            unsigned long long &lastmin) {
   if (!cta_own) return;
-  if (((i + 1) % KS == 0) || (i == H - 1)) {
+  if (((i + 1) % KSS == 0) || (i == H - 1)) {
     const uint32_t d = (uint32_t)(fb - c0 + 128);
     const uint32_t a = ((k[0] + d) & 0xFFu) | (((k[1] + d - 1u) & 0xFFu) << 8) | (((k[2] + d - 2u) & 0xFFu) << 16) |
                        (((k[3] + d - 3u) & 0xFFu) << 24);
-    if (gw) *reinterpret_cast<uint32_t *>(gat + (size_t)(i / KS) * gw + c0) = a;
-    else *reinterpret_cast<uint32_t *>(ancT + (size_t)(i / KS) * OWC + (c0 - A)) = a;
+    if (gw) *reinterpret_cast<uint32_t *>(gat + (size_t)(i / KSS) * gw + c0) = a;
+    else *reinterpret_cast<uint32_t *>(ancT + (size_t)(i / KSS) * OWC + (c0 - A)) = a;
   }
-  if (((i + 1) % KS == 0) && (i + 1 < H)) {
+  if (((i + 1) % KSS == 0) && (i + 1 < H)) {
     uint4 m;
     m.x = k[0] >> 8; m.y = k[1] >> 8; m.z = k[2] >> 8; m.w = k[3] >> 8;
-    *reinterpret_cast<uint4 *>(Mrow + (size_t)((i + 1) / KS) * pitch_e + c0) = m;
+    *reinterpret_cast<uint4 *>(Mrow + (size_t)((i + 1) / KSS) * pitch_e + c0) = m;
   }
   if (i == H - 1) {
 #pragma unroll
@@ -171,20 +176,36 @@ __device__ __forceinline__ uint32_t add_mask(uint32_t x, uint32_t e, uint32_t ma
 }
 
 // One DP row for a lane: keys k (previous row) -> next row; energies ev (4 x uint16).
-template <bool MASK>
+// LAT (a latency-bound search, one compute warp per SM sub-partition) takes, in warps without
+// excluded columns, the instruction forms that shorten the row's dependent chain at the price of
+// a few more instructions: the pairwise minima of the lane's own columns first (independent of
+// the neighbours' shuffled values), then the neighbour and the energy in one add-min
+// (min(a + e, b + e) = min(a, b) + e, exact: keys stay below 2^32 - e there). The
+// throughput-bound kernels (several warps per sub-partition) and the masked warps keep the
+// 3-input minimum.
+template <bool MASK, bool LAT = false>
 __device__ __forceinline__ void dp_row(uint32_t (&k)[V], uint2 ev, const uint32_t (&oobm)[V]) {
   const uint32_t e0 = lo8(ev.x), e1 = hi8(ev.x), e2 = lo8(ev.y), e3 = hi8(ev.y);
   const uint32_t L = __shfl_up_sync(0xffffffffu, k[V - 1], 1);
   const uint32_t R = __shfl_down_sync(0xffffffffu, k[0], 1);
-  const uint32_t n0 = add_mask<MASK>(min3u(L, k[0], k[1]), e0, oobm[0]);
-  const uint32_t n1 = add_mask<MASK>(min3u(k[0], k[1], k[2]), e1, oobm[1]);
-  const uint32_t n2 = add_mask<MASK>(min3u(k[1], k[2], k[3]), e2, oobm[2]);
-  const uint32_t n3 = add_mask<MASK>(min3u(k[2], k[3], R), e3, oobm[3]);
+  uint32_t n0, n1, n2, n3;
+  if (LAT && !MASK) {
+    const uint32_t p01 = min(k[0], k[1]), p23 = min(k[2], k[3]);
+    n0 = __viaddmin_u32(L, e0, p01 + e0);
+    n1 = __viaddmin_u32(k[2], e1, p01 + e1);
+    n2 = __viaddmin_u32(k[1], e2, p23 + e2);
+    n3 = __viaddmin_u32(R, e3, p23 + e3);
+  } else {
+    n0 = add_mask<MASK>(min3u(L, k[0], k[1]), e0, oobm[0]);
+    n1 = add_mask<MASK>(min3u(k[0], k[1], k[2]), e1, oobm[1]);
+    n2 = add_mask<MASK>(min3u(k[1], k[2], k[3]), e2, oobm[2]);
+    n3 = add_mask<MASK>(min3u(k[2], k[3], R), e3, oobm[3]);
+  }
   k[0] = n0; k[1] = n1; k[2] = n2; k[3] = n3;
 }
 
 // KT rows of a full tile from the staged energies er (row stride BW); MASK applies oobm.
-template <int KT, int BW, bool MASK>
+template <int KT, int BW, bool MASK, bool LAT = false>
 __device__ __forceinline__ void dp_rows(uint32_t (&k)[V], const uint16_t *er, const uint32_t (&oobm)[V]) {
   uint2 a = *reinterpret_cast<const uint2 *>(er);
   uint2 b = *reinterpret_cast<const uint2 *>(er + BW);
@@ -193,13 +214,13 @@ __device__ __forceinline__ void dp_rows(uint32_t (&k)[V], const uint16_t *er, co
     const uint2 ev = a;
     a = b;
     if (r + 2 < KT) b = *reinterpret_cast<const uint2 *>(er + (r + 2) * BW);
-    dp_row<MASK>(k, ev, oobm);
+    dp_row<MASK, LAT>(k, ev, oobm);
   }
 }
 
 // Rows rb .. n-1 (n <= KT) of a tile: the first tile (rb = 1, row 0 initialises) or a ragged
 // last tile, at the pace of a full tile.
-template <int KT, int BW, bool MASK>
+template <int KT, int BW, bool MASK, bool LAT = false>
 __device__ __forceinline__ void dp_rows_n(uint32_t (&k)[V], const uint16_t *er, const uint32_t (&oobm)[V], int rb,
                                           int n) {
   uint2 a = *reinterpret_cast<const uint2 *>(er + rb * BW);
@@ -210,7 +231,7 @@ __device__ __forceinline__ void dp_rows_n(uint32_t (&k)[V], const uint16_t *er, 
     const uint2 ev = a;
     a = b;
     if (r + 2 < n) b = *reinterpret_cast<const uint2 *>(er + (r + 2) * BW);
-    dp_row<MASK>(k, ev, oobm);
+    dp_row<MASK, LAT>(k, ev, oobm);
   }
 }
 
@@ -257,9 +278,9 @@ __device__ __forceinline__ void dp_rows_n_fwd(uint32_t (&k)[V], const uint16_t *
 
 // Initialise the staging and halo mbarriers (thread 0; the caller then synchronises the CTA, and
 // the cluster when CL).
-template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false>
+template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false, int KSS = KS>
 __device__ inline void search_init(unsigned char *smem, int S) {
-  const SearchPlan plan = search_plan<NW, KT, CL, FWM, FWD>(S);
+  const SearchPlan plan = search_plan<NW, KT, CL, FWM, FWD, KSS>(S);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + plan.bars);
   uint64_t *empty = full + NSLOT;
   uint64_t *hbar = empty + NSLOT;
@@ -281,18 +302,21 @@ __device__ __forceinline__ void group_sync() {
 
 // The search. Every thread of the CTA (of every CTA of the cluster when CL) calls it with the same
 // arguments; `Smax` is the super-tile count the shared-memory plan was sized for.
-template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false>
+template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false, int KSS = KS>
 __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, SearchState &st) {
   constexpr int NP = FWD ? 3 : 1;   // cost planes staged per row
-  using G = Geo<NW, KT, CL, FWM>;
+  // the single-map search: one cluster, a CTA per SM, every compute warp alone on its SM
+  // sub-partition with 4 warps (latency-bound)
+  constexpr bool LAT = CL && FWM >= FILL_WARPS_MAX && NW == 4;
+  using G = Geo<NW, KT, CL, FWM, KSS>;
   constexpr int Q = G::Q, BW = G::BW, OWC = G::OWC, K2E = G::K2E;
   const int rank = CL ? (int)cg::this_cluster().block_rank() : 0;
   const int cs = CL ? (int)cg::this_cluster().num_blocks() : 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool producer = (warp == NW);
   const int H = p.H, W = p.W;
-  const int S = (H + KS - 1) / KS;
-  const SearchPlan plan = search_plan<NW, KT, CL, FWM, FWD>(Smax);
+  const int S = (H + KSS - 1) / KSS;
+  const SearchPlan plan = search_plan<NW, KT, CL, FWM, FWD, KSS>(Smax);
   uint32_t *bnd = reinterpret_cast<uint32_t *>(smem + plan.bnd);
   uint32_t *hbuf = reinterpret_cast<uint32_t *>(smem + plan.hbuf);
   uint8_t *ancT = reinterpret_cast<uint8_t *>(smem + plan.anc);
@@ -314,7 +338,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   const int ext0 = A - K2E;                     // extended range start
   const int own0 = ext0 + warp * Q;             // warp strip start
   const int c0 = own0 - KT + lane * V;          // this lane's first column
-  const int frame_base = own0 - KS;             // ancestor frame of this warp
+  const int frame_base = own0 - KSS;            // ancestor frame of this warp
   const bool strip_lane = !producer && (lane * V >= KT) && (lane * V < KT + Q);
   const bool cta_own = strip_lane && c0 >= A && c0 < B;   // A, B, c0 are multiples of 4
   uint32_t oobm[V];
@@ -387,7 +411,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
           // At a new super-tile every cell becomes its own ancestor; the old ancestor field is
           // dropped without arithmetic (it may lie outside this warp's frame).
           const uint4 v = *reinterpret_cast<const uint4 *>(bnd + ((t - 1) & 1) * BW + bidx0);
-          const bool fresh = (r0 % KS) == 0;
+          const bool fresh = (r0 % KSS) == 0;
           const uint32_t d = own_a - 128u;
           k[0] = fresh ? ((v.x & ~0xFFu) | own_a) : (v.x + d);
           k[1] = fresh ? ((v.y & ~0xFFu) | (own_a + 1u)) : (v.y + d + 1u);
@@ -400,16 +424,16 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
           // the row that needs them, off the dependent chain); bookkeeping only where a
           // super-tile or the image ends on its last row
           if (FWD) dp_rows_fwd<KT, BW, EDGE>(k, er, oobm);
-          else dp_rows<KT, BW, EDGE>(k, er, oobm);
+          else dp_rows<KT, BW, EDGE, LAT>(k, er, oobm);
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[slot]);   // this warp is done with the staged rows
-          if (((r0 + KT) % KS) == 0 || r0 + KT == H)
-            row_events(r0 + KT - 1, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, gat0, gw, lastmin);
+          if (((r0 + KT) % KSS) == 0 || r0 + KT == H)
+            row_events<KSS>(r0 + KT - 1, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, gat0, gw, lastmin);
         } else {
           // first tile (row 0 has no predecessor) or a ragged last tile. Neither holds a row with
-          // bookkeeping except the image's last row: a super-tile ends on a multiple of KS (a
-          // multiple of KT), which is never inside these tiles' rows 0 .. n-1 (n < KT for the
-          // ragged tile; the first tile ends at row KT-1 < KS-1)
+          // bookkeeping except the image's last row and the first tile's last row when KSS = KT:
+          // a super-tile ends on a multiple of KSS (a multiple of KT), which is never inside
+          // these tiles' rows 0 .. n-2
           const int n = (H - r0 < KT) ? H - r0 : KT;
           if (t == 0) {
             const uint2 ev = *reinterpret_cast<const uint2 *>(er);   // CU with FWD
@@ -419,11 +443,11 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
             k[3] = (hi8(ev.y) | (own_a + 3u)) | oobm[3];
           }
           if (FWD) dp_rows_n_fwd<KT, BW, EDGE>(k, er, oobm, t == 0 ? 1 : 0, n);
-          else dp_rows_n<KT, BW, EDGE>(k, er, oobm, t == 0 ? 1 : 0, n);
+          else dp_rows_n<KT, BW, EDGE, LAT>(k, er, oobm, t == 0 ? 1 : 0, n);
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[slot]);
-          if (((r0 + n) % KS) == 0 || r0 + n == H)
-            row_events(r0 + n - 1, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, gat0, gw, lastmin);
+          if (((r0 + n) % KSS) == 0 || r0 + n == H)
+            row_events<KSS>(r0 + n - 1, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, gat0, gw, lastmin);
         }
         if (more) {
           const bool exch = CL && ((r0 + KT) % K2 == 0) && cs > 1;
@@ -489,10 +513,17 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
     for (int r = 0; r < cs; ++r) best = cmin[r] < best ? cmin[r] : best;
     int j = (int)(best & 0xFFFFFFFFull);
     if (ok && (j < 0 || j >= W)) { ok = 0; atomicOr(p.err, ERR_BAD_SEAM); }
-    for (int s = S - 1; ok && gw && s >= 0; --s) {
-      jb[s] = j;
-      j = j + (int)gat[(size_t)s * gw + j] - 128;
-      if (j < 0 || j >= W) { ok = 0; atomicOr(p.err, ERR_BAD_SEAM); }
+    if (ok && gw) {
+      // branch-free hops: a column outside the map is clamped (every table read stays inside
+      // the table) and recorded as a failure
+      bool bad = false;
+      for (int s = S - 1; s >= 0; --s) {
+        jb[s] = j;
+        const int nj = j + (int)gat[(size_t)s * gw + j] - 128;
+        bad |= (unsigned)nj >= (unsigned)W;
+        j = min(max(nj, 0), W - 1);
+      }
+      if (bad) { ok = 0; atomicOr(p.err, ERR_BAD_SEAM); }
     }
     for (int s = S - 1; ok && !gw && s >= 0; --s) {
       jb[s] = j;
@@ -509,97 +540,113 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   }
   group_sync<CL>();
 
-  // ---- parallel backtrack: each super-tile recomputed in a 256-column window ----
+  // ---- parallel backtrack: each super-tile recomputed in a FILLW-column window ----
+  // A path cell r rows into a super-tile lies within KSS - 1 - r columns of the bottom column
+  // jb[s], and its three predecessors depend on the saved row only within KSS columns of jb[s]:
+  // the window [x0, x0 + FILLW) with x0 = jb[s] - FILLW / 2 (rounded down to FV) holds them all.
+  constexpr int FV = G::FV, FILLW = G::FILLW;
+  // direction rows: 2 bits per column (FV = 8), or one byte per column (FV = 4: the walk then
+  // reads its column's byte directly)
+  using DirT = typename std::conditional<FV == 8, uint16_t, uint32_t>::type;
+  using EVec = typename std::conditional<FV == 8, uint4, uint2>::type;        // FV uint16 energies
+  constexpr int PST = 32 * (int)sizeof(DirT) / 4;   // 32-bit words per direction row
   const int *jb0 = CL ? cg::this_cluster().map_shared_rank(jb, 0) : jb;
   const int *misc0 = CL ? cg::this_cluster().map_shared_rank(misc, 0) : misc;
   const int ok = misc0[0];
   const uint32_t best_m = (uint32_t)misc0[1];
-  uint16_t *fd = fdir + (size_t)warp * KS * 32;
+  DirT *fd = reinterpret_cast<DirT *>(fdir) + (size_t)warp * KSS * 32;
   const uint16_t *const Ef = p.E;
   int32_t *const seam_out = p.seam;
   int32_t *const seam_log = p.seam_log;
   int *const errw = p.err;
-  // the energies of a super-tile's window (KS rows x FILL_W columns, two rows per lane) are
-  // prefetched into L2 one super-tile ahead: the map has usually left L2 since the DP pass read it
+  // the energies of a super-tile's window (KSS rows, two rows per lane at most) are prefetched
+  // into L2 one super-tile ahead: the map has usually left L2 since the DP pass read it. The
+  // prefetch starts on a 16-byte boundary and covers the window.
   auto prefetch_window = [&](int s) {
     if (s >= S) return;
-    int x0 = jb0[s] - 128;
+    int x0 = jb0[s] - FILLW / 2;
     x0 -= ((x0 % 8) + 8) % 8;
-    for (int i = s * KS + lane; i < s * KS + KS && i < H; i += 32)
+    for (int i = s * KSS + lane; i < s * KSS + KSS && i < H; i += 32)
 #pragma unroll
-      for (int pl = 0; pl < NP; ++pl) bulk_prefetch_l2(Ef + pl * pstride + (size_t)i * pitch_e + x0, FILL_W * 2);
+      for (int pl = 0; pl < NP; ++pl) bulk_prefetch_l2(Ef + pl * pstride + (size_t)i * pitch_e + x0, FILLW * 2 + 16);
+  };
+  auto unpack = [](const EVec &v, uint32_t (&x)[FV]) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(&v);
+#pragma unroll
+    for (int q = 0; q < FV / 2; ++q) {
+      x[2 * q] = w[q] & 0xFFFFu;
+      x[2 * q + 1] = w[q] >> 16;
+    }
   };
   if (ok && warp < G::FW) prefetch_window(warp * cs + rank);
   for (int s = warp * cs + rank; ok && warp < G::FW && s < S; s += G::FW * cs) {
     prefetch_window(s + G::FW * cs);
     const int jbs = jb0[s];
     const int jprev = (s > 0) ? jb0[s - 1] : jb0[S];
-    int x0 = jbs - 128;
-    x0 -= ((x0 % 8) + 8) % 8;
-    const int xc = x0 + lane * 8;
-    const int rs = s * KS, re = (rs + KS < H) ? rs + KS : H;
+    int x0 = jbs - FILLW / 2;
+    x0 -= ((x0 % FV) + FV) % FV;
+    const int xc = x0 + lane * FV;
+    const int rs = s * KSS, re = (rs + KSS < H) ? rs + KSS : H;
     const int first = (s == 0) ? 1 : rs;
-    uint32_t m[8], oob[8];
+    uint32_t m[FV], oob[FV];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) oob[u] = (xc + u < 0 || xc + u >= W) ? SENT : 0u;
+    for (int u = 0; u < FV; ++u) oob[u] = (xc + u < 0 || xc + u >= W) ? SENT : 0u;
     if (s == 0) {
-      const uint4 ev = *reinterpret_cast<const uint4 *>(Ef + xc);
-      m[0] = ev.x & 0xFFFFu; m[1] = ev.x >> 16; m[2] = ev.y & 0xFFFFu; m[3] = ev.y >> 16;
-      m[4] = ev.z & 0xFFFFu; m[5] = ev.z >> 16; m[6] = ev.w & 0xFFFFu; m[7] = ev.w >> 16;
+      unpack(*reinterpret_cast<const EVec *>(Ef + xc), m);
     } else {
-      const uint4 a = *reinterpret_cast<const uint4 *>(Mrow + (size_t)s * pitch_e + xc);
-      const uint4 b = *reinterpret_cast<const uint4 *>(Mrow + (size_t)s * pitch_e + xc + 4);
-      m[0] = a.x; m[1] = a.y; m[2] = a.z; m[3] = a.w; m[4] = b.x; m[5] = b.y; m[6] = b.z; m[7] = b.w;
+#pragma unroll
+      for (int q = 0; q < FV / 4; ++q) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(Mrow + (size_t)s * pitch_e + xc + 4 * q);
+        m[4 * q] = a.x; m[4 * q + 1] = a.y; m[4 * q + 2] = a.z; m[4 * q + 3] = a.w;
+      }
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) m[u] |= oob[u];
+    for (int u = 0; u < FV; ++u) m[u] |= oob[u];
     // rows first..re-1 in chunks with the next chunk's energies loaded ahead. The single-map
     // search (all fill warps, one CTA per SM, latency-bound) has registers to spare for 8-row
     // chunks, whose compute covers an L2 round trip; the batched and multi-map kernels, whose
     // latency other CTAs hide and whose registers are capped, use 2-row chunks.
     constexpr int CH = FWD ? 2 : ((CL && FWM >= FILL_WARPS_MAX) ? 8 : 2);
-    uint4 eb0[NP][CH], eb1[NP][CH];
-    auto load_chunk = [&](uint4 (&eb)[NP][CH], int rbeg) {
+    EVec eb0[NP][CH], eb1[NP][CH];
+    auto load_chunk = [&](EVec (&eb)[NP][CH], int rbeg) {
 #pragma unroll
       for (int r = 0; r < CH; ++r) {
         const int i = rbeg + r;
 #pragma unroll
         for (int pl = 0; pl < NP; ++pl)
-          if (i < re) eb[pl][r] = *reinterpret_cast<const uint4 *>(Ef + pl * pstride + (size_t)i * pitch_e + xc);
+          if (i < re) eb[pl][r] = *reinterpret_cast<const EVec *>(Ef + pl * pstride + (size_t)i * pitch_e + xc);
       }
     };
-    auto unpack8 = [](const uint4 &v, uint32_t (&x)[8]) {
-      x[0] = v.x & 0xFFFFu; x[1] = v.x >> 16; x[2] = v.y & 0xFFFFu; x[3] = v.y >> 16;
-      x[4] = v.z & 0xFFFFu; x[5] = v.z >> 16; x[6] = v.w & 0xFFFFu; x[7] = v.w >> 16;
-    };
-    auto run_chunk = [&](const uint4 (&eb)[NP][CH], int rbeg) {
+    auto run_chunk = [&](const EVec (&eb)[NP][CH], int rbeg) {
 #pragma unroll
       for (int r = 0; r < CH; ++r) {
         const int i = rbeg + r;
         if (i >= re) break;
-        uint32_t ee[8], dl[8] = {0, 0, 0, 0, 0, 0, 0, 0}, dr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        unpack8(eb[0][r], ee);
+        uint32_t ee[FV], dl[FV], dr[FV];
+#pragma unroll
+        for (int u = 0; u < FV; ++u) dl[u] = dr[u] = 0u;
+        unpack(eb[0][r], ee);
         if (FWD) {
-          unpack8(eb[NP > 1 ? 1 : 0][r], dl);
-          unpack8(eb[NP > 2 ? 2 : 0][r], dr);
+          unpack(eb[NP > 1 ? 1 : 0][r], dl);
+          unpack(eb[NP > 2 ? 2 : 0][r], dr);
         }
-        const uint32_t L = __shfl_up_sync(0xffffffffu, m[7], 1);
+        const uint32_t L = __shfl_up_sync(0xffffffffu, m[FV - 1], 1);
         const uint32_t R = __shfl_down_sync(0xffffffffu, m[0], 1);
-        uint32_t nm[8];
+        uint32_t nm[FV];
         uint32_t dirs = 0;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < FV; ++u) {
           const uint32_t a = ((u == 0) ? L : m[u - 1]) + dl[u];
           const uint32_t b = m[u];
-          const uint32_t c = ((u == 7) ? R : m[u + 1]) + dr[u];
+          const uint32_t c = ((u == FV - 1) ? R : m[u + 1]) + dr[u];
           const uint32_t mn = min3u(a, b, c);
           const uint32_t dd = (a == mn) ? 0u : ((b == mn) ? 1u : 2u);
-          dirs |= dd << (2 * u);
+          dirs |= dd << ((FV == 4 ? 8 : 2) * u);
           nm[u] = add_mask<true>(mn, ee[u], oob[u]);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) m[u] = nm[u];
-        fd[(i - rs) * 32 + lane] = (uint16_t)dirs;
+        for (int u = 0; u < FV; ++u) m[u] = nm[u];
+        fd[(i - rs) * 32 + lane] = (DirT)dirs;
       }
     };
     int rb = first;
@@ -616,43 +663,55 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
     if (s == S - 1) {
       // the recomputed cost at the bottom of the seam must be the argmin's
       const int rel = jbs - x0;
-      if ((rel >> 3) == lane) {
+      if (rel / FV == lane) {
         uint32_t v = 0;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) if (u == (rel & 7)) v = m[u];
+        for (int u = 0; u < FV; ++u) if (u == rel % FV) v = m[u];
         if (v != best_m) atomicOr(errw, ERR_COST_MISMATCH);
       }
     }
     __syncwarp();
     // lane 0 follows the directions up the window (relative columns, kept in the direction rows it
     // has read: a row's entry is not needed again), then the warp writes the seam rows
-    uint32_t *path = reinterpret_cast<uint32_t *>(fd);   // fd[(i - rs) * 32] holds the column of row i
+    uint32_t *path = reinterpret_cast<uint32_t *>(fd);   // path[(i - rs) * PST] holds the column of row i
     if (lane == 0) {
       int rel = jbs - x0;
       bool okp = true;
-      for (int i = re - 1; i >= first; --i) {
-        if (rel < 0 || rel >= FILL_W) { okp = false; break; }
-        const uint32_t dd = (fd[(i - rs) * 32 + (rel >> 3)] >> (2 * (rel & 7))) & 3u;
-        path[(i - rs) * 16] = (uint32_t)rel;   // the first 4 bytes of row i's direction words
-        rel += (int)dd - 1;
+      if constexpr (FV == 4) {
+        // one byte per column; a step leaving the window is clamped (every read stays in this
+        // warp's rows) and recorded as a failure
+        const uint8_t *fb = reinterpret_cast<const uint8_t *>(fd) + (size_t)(re - 1 - rs) * FILLW;
+        for (int i = re - 1; i >= first; --i, fb -= FILLW) {
+          const int nr = rel + (int)fb[rel] - 1;
+          path[(i - rs) * PST] = (uint32_t)rel;   // the first 4 bytes of row i's direction words
+          okp &= (unsigned)nr < (unsigned)FILLW;
+          rel = min(max(nr, 0), FILLW - 1);
+        }
+      } else {
+        for (int i = re - 1; i >= first; --i) {
+          if (rel < 0 || rel >= FILLW) { okp = false; break; }
+          const uint32_t dd = ((uint32_t)fd[(i - rs) * 32 + rel / FV] >> (2 * (rel % FV))) & 3u;
+          path[(i - rs) * PST] = (uint32_t)rel;   // the first 4 bytes of row i's direction words
+          rel += (int)dd - 1;
+        }
       }
       if (!okp) {
         atomicOr(errw, ERR_FILL_MISMATCH);
         rel = -1 - x0;
       }
-      path[KS * 16 - 1] = (uint32_t)rel;    // the column above row `first` (row 0's seam when s == 0)
+      path[KSS * PST - 1] = (uint32_t)rel;    // the column above row `first` (row 0's seam when s == 0)
       if (x0 + rel != jprev) atomicOr(errw, ERR_FILL_MISMATCH);
     }
     __syncwarp();
-    const bool path_ok = (int)path[KS * 16 - 1] + x0 >= 0;
+    const bool path_ok = (int)path[KSS * PST - 1] + x0 >= 0;
     if (path_ok) {
       for (int i = first + lane; i < re; i += 32) {
-        const int j = x0 + (int)path[(i - rs) * 16];
+        const int j = x0 + (int)path[(i - rs) * PST];
         seam_out[i] = j;
         if (seam_log) seam_log[i] = j;
       }
       if (s == 0 && lane == 0) {
-        const int j = x0 + (int)path[KS * 16 - 1];
+        const int j = x0 + (int)path[KSS * PST - 1];
         seam_out[0] = j;
         if (seam_log) seam_log[0] = j;
       }
