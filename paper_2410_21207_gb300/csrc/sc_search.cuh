@@ -606,7 +606,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
     // search (all fill warps, one CTA per SM, latency-bound) has registers to spare for 8-row
     // chunks, whose compute covers an L2 round trip; the batched and multi-map kernels, whose
     // latency other CTAs hide and whose registers are capped, use 2-row chunks.
-    constexpr int CH = FWD ? 2 : ((CL && FWM >= FILL_WARPS_MAX) ? 8 : 2);
+    constexpr int CH = FWD ? 2 : ((CL && FWM >= FILL_WARPS_MAX) ? (FV == 4 ? 16 : 8) : 2);
     EVec eb0[NP][CH], eb1[NP][CH];
     auto load_chunk = [&](EVec (&eb)[NP][CH], int rbeg) {
 #pragma unroll
