@@ -170,7 +170,7 @@ static int ensure_carve_buffers(Workspace &ws, int H, int W) {
   SC_CUDA(ws.img2.ensure((size_t)R * P));
   const int pe = pitch_e_for(R);
   SC_CUDA(ws.E.ensure((size_t)R * pe));
-  const int S = (R + KS_MIN - 1) / KS_MIN;
+  const int S = (R + KS - 1) / KS;
   SC_CUDA(ws.Mrow.ensure((size_t)(S + 1) * pe));
   SC_CUDA(ws.seam.ensure((size_t)R));
   SC_CUDA(ws.lists.ensure((size_t)2 * R * RPEND));
@@ -411,7 +411,7 @@ int sc_find_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_
   if ((rc = ensure_flags(ws, st))) return rc;
   const int pe = pitch_e_for(W);
   SC_CUDA(ws.E.ensure((size_t)H * pe));
-  SC_CUDA(ws.Mrow.ensure((size_t)((H + KS_MIN - 1) / KS_MIN + 1) * pe));
+  SC_CUDA(ws.Mrow.ensure((size_t)((H + KS - 1) / KS + 1) * pe));
   SC_CUDA(cudaMemsetAsync(ws.flags.p + 1, 0, sizeof(int), st));
   SC_CUDA(launch_copy_energy(energy, H, W, ws.E.p + E_PADL, pe, ws.flags.p, ws.flags.p + 1, st));
   return launch_search(ws, ws.E.p, pe, H, W, seam_out, nullptr, cost_out, ws.flags.p + 1, st);
@@ -508,7 +508,7 @@ int sc_find_seam_forward(const uint16_t *cu, const uint16_t *dl, const uint16_t 
   const int pe = pitch_e_for(W);
   const int64_t pstride = (int64_t)H * pe;
   SC_CUDA(ws.E.ensure((size_t)3 * H * pe));
-  SC_CUDA(ws.Mrow.ensure((size_t)((H + KS_MIN - 1) / KS_MIN + 1) * pe));
+  SC_CUDA(ws.Mrow.ensure((size_t)((H + KS - 1) / KS + 1) * pe));
   SC_CUDA(cudaMemsetAsync(ws.flags.p + 1, 0, sizeof(int), st));
   SC_CUDA(launch_copy_planes(cu, dl, dr, H, W, ws.E.p + E_PADL, pe, pstride, ws.flags.p, ws.flags.p + 1, st));
   return launch_search(ws, ws.E.p, pe, H, W, seam_out, nullptr, cost_out, ws.flags.p + 1, st, pstride);

@@ -27,11 +27,11 @@ DpShape dp_shape_for(int W) {
   return s;
 }
 
-// Super-tile height: 32 rows for the 4-warp shape, whose every CTA has an SM to itself and whose
-// backtrack fill (KSS rows, serial) then halves; 64 rows for the wide shapes, whose ancestor chain
-// crosses CTAs (one DSMEM load per super-tile) and would double.
+// Super-tile height: KS (32) rows for the 4-warp shape, whose ancestor chain is local (the table is
+// gathered in rank 0) and whose serial backtrack fill halves against 64; KS_WIDE (64) for the wide
+// shapes and forward energy, whose chain hops cross CTAs through DSMEM and would double.
 template <int NW, int KT, bool FWD>
-__host__ __device__ constexpr int dp_super_rows() { return (NW == 4 && KT == 32 && !FWD) ? KS_MIN : KS; }
+__host__ __device__ constexpr int dp_super_rows() { return (NW == 4 && KT == 32 && !FWD) ? KS : KS_WIDE; }
 
 template <int NW, int KT, bool FWD = false>
 __global__ void __launch_bounds__(Geo<NW, KT, true>::THREADS, 1) k_dp(DpArgs p) {

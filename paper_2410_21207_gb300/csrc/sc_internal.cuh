@@ -20,11 +20,13 @@ constexpr int E_PADR = 1024;   // right pad (elements)
 // Seam-search geometry (sc_search.cuh). A lane owns V consecutive columns; a warp's window is
 // 32*V columns, of which 32*V - 2*KT are its own strip; windows exchange boundary rows every KT
 // rows inside a CTA (shared memory) and every K2 rows between the CTAs of a cluster (DSMEM).
-// Ancestors are tracked over super-tiles of KS rows (KS_MIN for the single-map 4-warp search,
-// whose backtrack fill is on the latency path). KT is a template parameter of each kernel.
+// Ancestors are tracked over super-tiles of KS rows; the single-map search of maps wider than a
+// 4-warp cluster covers uses KS_WIDE (its ancestor chain reads other CTAs through DSMEM, one load per
+// super-tile). Buffers of saved cost rows are sized for KS, the shorter. KT is a template
+// parameter of each kernel.
 constexpr int V = 4;
-constexpr int KS = 64;
-constexpr int KS_MIN = 32;   // buffers of saved cost rows are sized for super-tiles this short
+constexpr int KS = 32;
+constexpr int KS_WIDE = 64;
 constexpr int K2 = 64;
 constexpr int MAX_CLUSTER = 16;
 

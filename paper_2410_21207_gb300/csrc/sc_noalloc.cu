@@ -43,7 +43,7 @@ extern "C" int sc_find_seam_static(const uint16_t *energy, int H, int W, int32_t
   if (!energy || !seam_out) return SC_EINVAL;
   if (H < 1 || W < 1 || H > SC_MAX_ROWS || W > SC_MAX_COLS) return SC_EINVAL;
   const int pe = pitch_e_for(W);
-  const int S = (H + KS_MIN - 1) / KS_MIN;
+  const int S = (H + KS - 1) / KS;
   const size_t off_flags = 0;
   const size_t off_E = 256;
   const size_t off_M = off_E + align256((size_t)H * pe * sizeof(uint16_t));

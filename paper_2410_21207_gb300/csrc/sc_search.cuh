@@ -14,8 +14,8 @@
 //     columns on either side of its own range and every K2 rows pushes its edge columns into the
 //     neighbours' shared memory with st.async; there is no cluster-wide barrier in the row loop.
 //   * A cost travels with an ancestor: key = (M << 8) | a, with a the column (in the warp's frame)
-//     where the cell's optimal path crossed the top of the current super-tile of KSS rows (64, or
-//     32 for the latency-bound single-map search, whose backtrack fill then halves). The
+//     where the cell's optimal path crossed the top of the current super-tile of KSS rows (32; 64
+//     for the single-map search of wide maps, whose chain hops cross CTAs through DSMEM). The
 //     unsigned minimum of three keys is the minimum M and, among equal M, the smallest ancestor.
 //     Optimal predecessors never cross under the leftmost tie-break (pred(j) <= pred(j+1): if
 //     pred(j) = j+1 then M(j+1) < M(j), so j+1 cannot pick j), hence ancestors are non-decreasing
@@ -394,17 +394,17 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
     auto tiles = [&](auto edge_tag) {
       constexpr bool EDGE = decltype(edge_tag)::value;
       const uint32_t own_a = (uint32_t)(c0 - frame_base);   // this lane's first column, warp frame
-      bool ready = false;                                    // next tile's rows already tested staged
       for (int t = 0; t < nt; ++t) {
         const int r0 = t * KT;
         const bool more = r0 + KT < H;
         const uint32_t g = st.tiles + t;
         const int slot = (int)(g % NSLOT);
-        if (!ready && !mbar_wait_bounded(&full[slot], (g / NSLOT) & 1u, WAIT_TIMEOUT_NS)) {
+        // one barrier test per tile: the tile was issued NSLOT - 1 tiles ago and has landed by now
+        // (an earlier test of the next tile, overlapped with this tile's rows, found it still in
+        // flight every time and cost more than it saved)
+        if (!mbar_wait_bounded(&full[slot], (g / NSLOT) & 1u, WAIT_TIMEOUT_NS)) {
           if (lane == 0) atomicOr(p.err, ERR_TIMEOUT);
         }
-        // test the next tile's staging now: the answer is needed only at the next tile boundary
-        ready = more && mbar_test_wait(&full[(g + 1) % NSLOT], ((g + 1) / NSLOT) & 1u);
         const uint16_t *er = ring + (size_t)slot * NP * KT * BW + bidx0;
         if (t > 0) {
           // window of the previous row from the boundary buffer (relative ancestors -> warp frame).
