@@ -85,6 +85,34 @@ def test_find_seam_energy_range_rejected(dev):
     sc.check()   # cleared
 
 
+@pytest.mark.parametrize("H,W,lo,hi", [
+    (100, 1000, 0, 60000),      # energies far above any image energy
+    (100, 2000, 4090, 4100),    # a narrow band of large energies (near ties)
+    (3000, 300, 3000, 4095),    # tall map, costs near 2^23.5
+    (4096, 200, 3800, 4095),    # costs within 2^20 of the 2^24 cost limit
+    (64, 129, 4094, 4095),      # one value everywhere: all ties
+])
+def test_find_seam_large_costs(dev, H, W, lo, hi):
+    """Maps with large energies and costs close to the 24-bit cost field's limit, several CTAs
+    wide, equal to the oracle (seam and cost)."""
+    rng = np.random.default_rng(H * 31 + W + lo)
+    e = rng.integers(lo, hi, size=(H, W), endpoint=False).astype(np.uint16)
+    seam, cost = sc.find_seam(_to_dev(e, dev))
+    sc.check()
+    s_ref, c_ref = oracle.dp_seam(e)
+    assert int(_np(cost)[0]) == c_ref
+    np.testing.assert_array_equal(_np(seam), s_ref)
+
+
+def test_carve_max_energy_checkerboard(dev):
+    """A 4-channel 0/255 checkerboard: every e1 energy at its maximum (2040) and ties everywhere,
+    several CTAs wide, both passes."""
+    H, W = 160, 700
+    yy, xx = np.mgrid[0:H, 0:W]
+    img = (((yy + xx) & 1) * 255).astype(np.uint8)[:, :, None].repeat(4, axis=2)
+    _carve_cmp(dev, img, W - 40, H - 12)
+
+
 def _carve_ref(img, tw, th):
     return oracle.carve(img, tw, th, with_log=True)
 
