@@ -28,9 +28,15 @@ __device__ __forceinline__ uint32_t energy_at(const uint32_t *img, int pitch, in
 // before any lane of the warp writes. The first chunk keeps its elements left of s. Elements from
 // W-1 to the end of the last chunk are left undefined (they lie in the row's padding or in the
 // column that the shift drops).
-__device__ __forceinline__ void shift_row_u16(uint16_t *row, int s, int W, int lane) {
+// `between` runs once, after the first block of loads is issued and before any store (work that
+// overlaps their latency; it must not touch the row).
+template <typename F>
+__device__ __forceinline__ void shift_row_u16(uint16_t *row, int s, int W, int lane, F &&between) {
   constexpr int R = 4;
-  if (s >= W - 1) return;
+  if (s >= W - 1) {
+    between();
+    return;
+  }
   const int c_lo = s >> 3, c_hi = (W - 2) >> 3;
   for (int cb = c_lo; cb <= c_hi; cb += 32 * R) {
     uint4 x[R];
@@ -43,6 +49,7 @@ __device__ __forceinline__ void shift_row_u16(uint16_t *row, int s, int W, int l
         nx[r] = row[8 * c + 8];
       }
     }
+    if (cb == c_lo) between();
     __syncwarp();
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -69,6 +76,10 @@ __device__ __forceinline__ void shift_row_u16(uint16_t *row, int s, int W, int l
     }
     __syncwarp();
   }
+}
+
+__device__ __forceinline__ void shift_row_u16(uint16_t *row, int s, int W, int lane) {
+  shift_row_u16(row, s, W, lane, [] {});
 }
 
 __device__ __forceinline__ uint32_t pack_pixel(const uint8_t *s, int C) {
@@ -188,14 +199,16 @@ __device__ __forceinline__ bool refresh_row(const uint32_t *img, int pitch, uint
   const int s = seam[i];
   if (s < 0 || s >= W) return false;
   uint32_t p = 0;
-  if (lane == 0) {
-    bool bad = false;
-    p = patch_row_lazy(img, pitch, H, W, seam, lists_in, m, i, &bad);
-    list_insert(lists_in + (int64_t)i * RPEND, lists_out + (int64_t)i * RPEND, m, s);
-  }
-  p = __shfl_sync(0xffffffffu, p, 0);
   uint16_t *er = E + (int64_t)i * pe;
-  shift_row_u16(er, s, W, lane);
+  // lane 0 computes the refreshed pair (image words through the lists, not the energy row) while
+  // the warp's loads of the energy tail are in flight
+  shift_row_u16(er, s, W, lane, [&] {
+    if (lane == 0) {
+      bool bad = false;
+      p = patch_row_lazy(img, pitch, H, W, seam, lists_in, m, i, &bad);
+      list_insert(lists_in + (int64_t)i * RPEND, lists_out + (int64_t)i * RPEND, m, s);
+    }
+  });
   if (lane == 0) {
     if (s >= 1) er[s - 1] = (uint16_t)(p & 0xFFFFu);
     if (s <= W - 2) er[s] = (uint16_t)(p >> 16);
