@@ -171,7 +171,7 @@ int sc_find_seam_multi_shape(int warps, int tile_rows);
  * 32 MiB inside the library's device image, held by every GPU that loads the library until the
  * process exits; the call never calls cudaMalloc or cudaFree.
  *   - Size limit: the map must fit the array, roughly H * (W + 1280) * 2 bytes plus one row of
- *     4-byte costs per 64 rows (3840 x 2160 fits). Larger maps return SC_EINVAL (a message naming
+ *     4-byte costs per 32 rows (3840 x 2160 fits). Larger maps return SC_EINVAL (a message naming
  *     the bytes needed goes to stderr), before any work is enqueued.
  *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress);
  *     make that first call before any stream capture.
