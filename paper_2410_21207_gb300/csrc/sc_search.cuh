@@ -603,9 +603,10 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
 #pragma unroll
     for (int u = 0; u < FV; ++u) m[u] |= oob[u];
     // rows first..re-1 in chunks with the next chunk's energies loaded ahead. The single-map
-    // search (all fill warps, one CTA per SM, latency-bound) has registers to spare for 8-row
-    // chunks, whose compute covers an L2 round trip; the batched and multi-map kernels, whose
-    // latency other CTAs hide and whose registers are capped, use 2-row chunks.
+    // search (all fill warps, one CTA per SM, latency-bound) has registers to spare for chunks
+    // whose compute covers an L2 round trip (16 rows of 4 columns per lane, 8 rows of 8); the
+    // batched and multi-map kernels, whose latency other CTAs hide and whose registers are
+    // capped, use 2-row chunks.
     constexpr int CH = FWD ? 2 : ((CL && FWM >= FILL_WARPS_MAX) ? (FV == 4 ? 16 : 8) : 2);
     EVec eb0[NP][CH], eb1[NP][CH];
     auto load_chunk = [&](EVec (&eb)[NP][CH], int rbeg) {
