@@ -607,7 +607,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
     // whose compute covers an L2 round trip (16 rows of 4 columns per lane, 8 rows of 8); the
     // batched and multi-map kernels, whose latency other CTAs hide and whose registers are
     // capped, use 2-row chunks.
-    constexpr int CH = FWD ? 2 : ((CL && FWM >= FILL_WARPS_MAX) ? (FV == 4 ? 16 : 8) : 2);
+    constexpr int CH = FWD ? 2 : ((CL && FWM >= FILL_WARPS_MAX) ? (FV == 4 ? 16 : 8) : (CL && FV == 4 ? 4 : 2));
     EVec eb0[NP][CH], eb1[NP][CH];
     auto load_chunk = [&](EVec (&eb)[NP][CH], int rbeg) {
 #pragma unroll
