@@ -12,7 +12,10 @@
 
 namespace sc {
 
-constexpr int MULTI_FILL_WARPS = 4;
+// backtrack-fill warps per CTA: 7 (of 9) gives the 68 super-tiles of a 2160-row map two fill rounds
+// on a 5-CTA cluster instead of four, with the direction rows still inside the idle staging ring;
+// below FILL_WARPS_MAX, so the throughput-bound forms of the search are kept (2-4-row chunks)
+constexpr int MULTI_FILL_WARPS = 7;
 
 template <int NW, int KT>
 __global__ void __launch_bounds__(Geo<NW, KT, true>::THREADS, NW == 8 ? 2 : 4) k_dp_multi(const DpArgs *__restrict__ ps) {
