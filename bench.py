@@ -11,12 +11,19 @@ outside the per-step CUDA-event brackets. Prints one JSON line (rank 0).
 Multi-GPU: every rank carves its own copy (replicas, weak scaling); value = all ranks' seams /
 the slowest rank's time. ``--impl reference`` times the oracle (plain C, host cores) on a bounded
 sample of the same workload.
+
+Besides the headline, rank 0 measures the other workloads (4K carve, 58 concurrent 4K searches,
+the 256-image batch, the serving trace: its first 300 requests against the plain path and all
+10,000 at their arrival times), an L2 copy peak for the L2 roofline fractions, and the oracle on
+the host cores for every configuration; a compact ``summary`` object is the line's last key.
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import platform
+import random
 import statistics
 import subprocess
 import sys
@@ -44,6 +51,11 @@ def _args():
     ap.add_argument("--no-4k", action="store_true", help="skip the 3840x2160 measurement")
     ap.add_argument("--no-paper", action="store_true", help="skip the paper's n x n workload points")
     ap.add_argument("--serving-requests", type=int, default=300)
+    ap.add_argument("--trace-requests", type=int, default=10000,
+                    help="requests of the full serving-trace replay (0 skips it)")
+    ap.add_argument("--profile-batch", metavar="N", type=int, default=None,
+                    help="only run the first N images of the batched workload through a batch plan twice "
+                         "(for ncu captures of k_batch)")
     ap.add_argument("--profile-search", metavar="HxW[xB]", default=None,
                     help="only call sc_find_seam a few times on a seeded HxW energy map, or sc_find_seam_multi "
                          "on B maps (for ncu captures)")
@@ -145,6 +157,52 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def cpu_info():
+    """Host cores and CPU model, printed beside every oracle timing."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"host_cores": os.cpu_count(), "cpu_model": model or platform.machine()}
+
+
+def l2_peak(torch, dev):
+    """Copy bandwidth with both buffers inside L2 (2 x 16 MiB against a 126 MB L2), repeated 50
+    times per CUDA-event bracket, best of 5: the denominator of the L2 roofline fractions (read +
+    write bytes per second)."""
+    n = 4 << 20   # float32 elements: 16 MiB
+    a = torch.ones(n, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    for _ in range(10):
+        b.copy_(a)
+    torch.cuda.synchronize(dev)
+    best = 0.0
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(50):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        best = max(best, 2 * 4 * n * 50 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    return best
+
+
 def _workload():
     from paper_2410_21207_gb300 import synth
     return synth.config2()
@@ -164,13 +222,66 @@ def cpu_baseline(job, img, budget_s: float = 15.0):
     mpix = sum(H * (W - t) for t in range(n)) / 1e6
     return {"value": n / dt, "unit": "seams/s", "mpix_seam_per_s": mpix / dt, "cores": 1, "kind": "oracle",
             "sample": f"first {n} of {W - job.target_w} seams of the {W}x{H} workload, single-threaded C, "
-                      f"full energy recompute per seam"}
+                      f"full energy recompute per seam", **cpu_info()}
 
 
-def batched_measurement(sc, torch, dev, flush, steps):
+def _oracle_carve_all(imgs, targets, threads):
+    """oracle.carve of every image, spread over `threads` host threads (the C calls release the
+    GIL), longest first; returns the wall time."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    order = sorted(range(len(imgs)), key=lambda k: -imgs[k].shape[0] * imgs[k].shape[1] *
+                   (imgs[k].shape[1] - targets[k][0] + imgs[k].shape[0] - targets[k][1]))
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda k: oracle.carve(imgs[k], *targets[k]), order))
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_configs(sample5):
+    """The oracle on the host cores for configurations 3, 4 and 5: config 3's 4K carve on one
+    thread over its first seams (bounded), the whole 256-image batch spread over all cores, and a
+    seeded 200-request sample of the serving trace spread over all cores."""
+    import oracle
+    from paper_2410_21207_gb300 import synth
+    info = cpu_info()
+    cores = info["host_cores"] or 1
+    out = dict(info)
+    job = synth.config3()
+    img = job.make()
+    t0 = time.perf_counter()
+    oracle.carve(img, job.W - 2, job.H)
+    per = (time.perf_counter() - t0) / 2
+    n = max(2, min(job.W - job.target_w, int(15.0 / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.carve(img, job.W - n, job.H)
+    dt = time.perf_counter() - t0
+    mpix = sum(job.H * (job.W - t) for t in range(n)) / 1e6
+    out["config3"] = {"seams_per_s": n / dt, "mpix_seam_per_s": mpix / dt, "threads": 1,
+                      "sample": f"first {n} of 960 vertical seams of the 3840x2160 image"}
+    jobs = synth.config4()
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        imgs = list(ex.map(lambda j: j.make(), jobs))
+    dt = _oracle_carve_all(imgs, [(j.target_w, j.target_h) for j in jobs], cores)
+    out["config4"] = {"seams_per_s": sum(j.seams for j in jobs) / dt,
+                      "mpix_seam_per_s": sum(j.mpix_seams() for j in jobs) / dt, "threads": cores,
+                      "sample": "all 256 images", "s": dt}
+    if sample5:
+        reqs = synth.config5()
+        idx = sorted(sample5)
+        dt = _oracle_carve_all([sample5[k] for k in idx], [(reqs[k].target_w, reqs[k].target_h) for k in idx], cores)
+        out["config5"] = {"req_per_s": len(idx) / dt, "seams_per_s": sum(reqs[k].seams for k in idx) / dt,
+                          "mpix_seam_per_s": sum(reqs[k].mpix_seams() for k in idx) / dt, "threads": cores,
+                          "sample": f"{len(idx)} requests drawn from the 10,000 (random.Random(5).sample)", "s": dt}
+    return out
+
+
+def batched_measurement(sc, torch, dev, flush, steps, peak, l2):
     """Config 4 (256 images, W 240..1280, H 180..960, width -10..40 %) as one autotuned batch plan
-    (persistent kernel in a CUDA graph) against the plain path (one image at a time, per-seam
-    launches) on the first 16 of the same images."""
+    (persistent kernels in a CUDA graph) against the plain path (one image at a time, per-seam
+    launches) on the same 256 images. Roofline of the batch graph (k_batch, plus k_batch_cl for
+    the images wider than one CTA): algorithmic bytes = 2.25 B per pixel of every searched map."""
     from paper_2410_21207_gb300 import synth
     jobs = synth.config4()
     imgs = [torch.from_numpy(j.make()).to(dev) for j in jobs]
@@ -178,11 +289,11 @@ def batched_measurement(sc, torch, dev, flush, steps):
     seams = sum(j.seams for j in jobs)
     mpix = sum(j.mpix_seams() for j in jobs)
     plan = sc.BatchPlan(imgs, targets, autotune=True)
-    for _ in range(2):
+    for _ in range(3):
         plan.run()
     sc.check()
     ms = []
-    for _ in range(max(2, steps)):
+    for _ in range(max(5, steps)):
         flush.zero_()
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
@@ -195,44 +306,80 @@ def batched_measurement(sc, torch, dev, flush, steps):
     info = plan.info()
     plan.close()
     bms = statistics.median(ms)
-    sub = list(range(16))
-    sub_seams = sum(jobs[k].seams for k in sub)
-    for k in sub[:2]:
+    for k in range(2):
         sc.carve(imgs[k], *targets[k], plain=True)
     torch.cuda.synchronize(dev)
     p0 = torch.cuda.Event(enable_timing=True)
     p1 = torch.cuda.Event(enable_timing=True)
     p0.record()
-    for k in sub:
+    for k in range(len(jobs)):
         sc.carve(imgs[k], *targets[k], plain=True)
     p1.record()
     torch.cuda.synchronize(dev)
     sc.check()
-    plain_sps = sub_seams / (p0.elapsed_time(p1) / 1000.0)
+    plain_sps = seams / (p0.elapsed_time(p1) / 1000.0)
     batched_sps = seams / (bms / 1000.0)
+    alg = 2.25 * mpix * 1e6
+    achieved = alg / (bms / 1000.0) / 1e9
     return {"workload": "256 images, W 240..1280, H 180..960, width -10..40 % (seed 4)",
             "seams_per_batch": seams, "ms_per_batch": bms, "seams_per_s": batched_sps,
             "mpix_seam_per_s": mpix / (bms / 1000.0), "plan": info,
-            "plain_seams_per_s": plain_sps, "plain_sample": "first 16 images, one image per launch sequence",
-            "batched_over_plain": batched_sps / plain_sps}
+            "plain_seams_per_s": plain_sps, "plain_sample": "all 256 images, one image per launch sequence",
+            "batched_over_plain": batched_sps / plain_sps,
+            "roofline": {"kernel": "k_batch graph (k_batch + k_batch_cl)", "bound": "hbm", "achieved": achieved,
+                         "unit": "GB/s", "peak": peak, "frac": achieved / peak, "l2_peak": l2,
+                         "l2_frac": achieved / l2 if l2 else None, "algorithmic_bytes_per_batch": alg,
+                         "traffic": _traffic_from_profile("k_batch_config4.txt"),
+                         "note": "the whole carve runs inside the graph; algorithmic bytes count the "
+                                 "energy+DP pass only (2.25 B per pixel per searched map)"}}
+
+
+_TRACE = {}
+TRACE_CANVASES = 8
+
+
+def _trace(n):
+    """The serving trace (cached per process: building all 10,000 requests takes a second or two)."""
+    from paper_2410_21207_gb300 import synth
+    if n not in _TRACE:
+        _TRACE[n] = synth.config5(n=n)
+    return _TRACE[n]
 
 
 def _gen_request(args):
     """Worker (spawned process): pixels of request k of the serving trace."""
     import sys as _sys
     _sys.path.insert(0, ROOT)
-    from paper_2410_21207_gb300 import synth
     k, n = args
-    return k, synth.config5(n=n)[k].make()
+    return k, _trace(n)[k].make()
 
 
-def pregenerate_serving(n):
-    """Images of the first n requests of the serving trace, made by a spawned process pool before
-    any GPU work in this process."""
+def _gen_canvas(k):
+    """Worker (spawned process): a 4096x2160 canvas of generator G (rectangles scaled by area, as
+    for every request) from which the full-trace replay crops its requests' pixels."""
+    import sys as _sys
+    _sys.path.insert(0, ROOT)
+    from paper_2410_21207_gb300 import synth
+    R, smin, smax = synth.scaled_rects(4096, 2160)
+    return synth.gen_image(4096, 2160, R, smin, smax, 50000 + k)
+
+
+def cpu_sample_indices():
+    """The seeded 200-request sample of the trace that the oracle is timed on."""
+    return sorted(random.Random(5).sample(range(10000), 200))
+
+
+def pregenerate(n_serving, canvases, sample):
+    """Pixels made by a spawned process pool before any GPU work in this process: the first
+    n_serving requests of the trace, the replay's canvases, and the oracle's request sample."""
     from multiprocessing import get_context
     procs = max(1, min(14, (os.cpu_count() or 2) - 2))
     with get_context("spawn").Pool(procs) as pool:
-        return dict(pool.map(_gen_request, [(k, n) for k in range(n)], chunksize=4))
+        serving = dict(pool.map(_gen_request, [(k, n_serving) for k in range(n_serving)], chunksize=4)) \
+            if n_serving else {}
+        canv = pool.map(_gen_canvas, range(TRACE_CANVASES)) if canvases else []
+        samp = dict(pool.map(_gen_request, [(k, 10000) for k in sample], chunksize=2)) if sample else {}
+    return serving, canv, samp
 
 
 def _pct(xs, q):
@@ -307,6 +454,68 @@ def serving_measurement(sc, torch, dev, imgs, n):
             "served_over_plain_throughput": plain_busy / cap_wall}
 
 
+def trace_replay_measurement(sc, torch, dev, canvases, n):
+    """All n requests of the serving trace (Poisson arrivals at 200 req/s, sizes log-uniform
+    128..4096 x 128..2160, targets 50..90 % x 80..100 %) submitted to sc_server (40 GB budget) at
+    their arrival times. Each request's size, targets and arrival come from the trace; its pixels
+    are a crop of one of the pre-generated canvases of generator G (making 10,000 images one by one
+    would take longer than the replay). Latency = completion - scheduled arrival; finished
+    requests are released as the replay goes, so host memory stays bounded."""
+    import numpy as np
+    reqs = _trace(10000)[:n]
+    seams = sum(r.seams for r in reqs)
+    mpix = sum(r.mpix_seams() for r in reqs)
+
+    def pixels(k, r):
+        c = canvases[k % len(canvases)]
+        x0 = (k * 7919) % (4096 - r.W + 1)
+        y0 = (k * 104729) % (2160 - r.H + 1)
+        return np.ascontiguousarray(c[y0:y0 + r.H, x0:x0 + r.W])
+
+    srv = sc.Server(budget_bytes=40 << 30, max_batch=64, streams=16)
+    for k in range(8):
+        srv.submit(pixels(k, reqs[k]), reqs[k].target_w, reqs[k].target_h)
+    srv.drain()
+    st0 = srv.stats()
+    outstanding = {}
+    lats = []
+
+    def collect():
+        for t in list(outstanding):
+            done, lat = srv.poll(t)
+            if done:
+                sub, arr = outstanding.pop(t)
+                lats.append(sub - arr + lat)
+                srv.release(t)
+
+    t0 = time.perf_counter()
+    late = 0
+    for k, r in enumerate(reqs):
+        delay = r.arrival_s - (time.perf_counter() - t0)
+        if delay > 0.002:
+            collect()
+            delay = r.arrival_s - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        else:
+            late += 1
+        sub = time.perf_counter() - t0
+        outstanding[srv.submit(pixels(k, r), r.target_w, r.target_h)] = (sub, r.arrival_s)
+    srv.drain(1800)
+    wall = time.perf_counter() - t0
+    collect()
+    st = srv.stats()
+    srv.close()
+    sc.check()
+    return {"workload": f"all {n} requests of the trace (seed 5) at their arrival times; pixels cropped from "
+                        f"{len(canvases)} generator-G canvases of 4096x2160",
+            "requests": len(lats), "wall_s": wall, "req_per_s": len(lats) / wall, "seams_per_s": seams / wall,
+            "mpix_seam_per_s": mpix / wall, "p50_ms": 1e3 * _pct(lats, 0.5), "p99_ms": 1e3 * _pct(lats, 0.99),
+            "max_ms": 1e3 * max(lats), "submitted_late": late,
+            "launch_groups": st["groups"] - st0["groups"], "peak_device_bytes": st["peak_bytes"],
+            "device_errors": st["device_errors"]}
+
+
 def fourk_measurement(sc, torch, dev, flush, steps):
     """Config 3: 3840x2160 -> 2880x1620 (960 vertical + 540 horizontal seams via transposition)."""
     from paper_2410_21207_gb300 import synth
@@ -315,7 +524,7 @@ def fourk_measurement(sc, torch, dev, flush, steps):
     sc.carve(img, job.target_w, job.target_h)
     torch.cuda.synchronize(dev)
     ms = []
-    for _ in range(max(1, min(2, steps))):
+    for _ in range(5):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -327,20 +536,20 @@ def fourk_measurement(sc, torch, dev, flush, steps):
     sc.check()
     t = statistics.median(ms) / 1000.0
     return {"workload": job.name, "seams_per_s": job.seams / t, "mpix_seam_per_s": job.mpix_seams() / t,
-            "ms_per_carve": 1e3 * t}
+            "ms_per_carve": 1e3 * t, "runs": len(ms)}
 
 
-def uhd_search_measurement(sc, torch, dev, steps, peak):
+def uhd_search_measurement(sc, torch, dev, steps, peak, l2):
     """The energy+DP pass at 3840x2160 with B independent maps in flight (one cluster each, B = how
     many fit on the GPU at once): the bandwidth view of the search, next to the single-map latency
-    chain. Algorithmic bytes = H*W*2.25 per map (energy read + one direction record)."""
-    import numpy as np
+    chain. Algorithmic bytes = H*W*2.25 per map (energy read + one direction record). The maps are
+    the e1 energy of config 3's image (sc_energy) and column rotations of it."""
     from paper_2410_21207_gb300 import synth
-    import oracle
     H, W = 2160, 3840
     B = max(1, sc.find_seam_multi_capacity(H, W))
-    e = oracle.energy(synth.config3().make()).astype(np.uint16)
-    maps = [torch.from_numpy(np.ascontiguousarray(np.roll(e, 37 * k, axis=1))).to(dev) for k in range(B)]
+    e = sc.energy(torch.from_numpy(synth.config3().make()).to(dev))
+    maps = [torch.roll(e, 37 * k, dims=1).contiguous() for k in range(B)]
+    sc.check()
     for _ in range(3):
         sc.find_seam_multi(maps)
     torch.cuda.synchronize(dev)
@@ -369,9 +578,11 @@ def uhd_search_measurement(sc, torch, dev, steps, peak):
             "kernel": "k_dp_multi", "kernel_us_per_launch": 1e6 * tk,
             "algorithmic_bytes_per_launch": alg, "achieved_gbs": alg / tk / 1e9,
             "peak_gbs": peak, "frac": alg / tk / 1e9 / peak if peak else None,
+            "l2_peak_gbs": l2, "l2_frac": alg / tk / 1e9 / l2 if l2 else None,
+            "call_gbs": alg / t / 1e9, "call_frac": alg / t / 1e9 / peak if peak else None,
             "traffic": _traffic_from_profile("k_dp_multi_3840x2160x58.txt") if B == 58 else None,
-            "note": "working set B x 16.6 MB exceeds L2, so no flush; the call also copies each map into "
-                    "its padded workspace (one extra kernel per map), the kernel figure excludes that"}
+            "note": "working set B x 16.6 MB exceeds L2, so no flush; the call figure includes everything "
+                    "the call enqueues, the kernel figure only k_dp_multi"}
 
 
 def forward_measurement(sc, torch, dev, img, tw, th, seams):
@@ -522,7 +733,7 @@ def run_reference(a):
         "config": {"workload": f"{job.name}; each step = the first {n} seams (bounded sample)",
                    "parallelism": "single-threaded CPU oracle"},
         "cpu_baseline": {"value": value, "unit": "seams/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {n} of {W - job.target_w} seams per step"},
+                         "sample": f"first {n} of {W - job.target_w} seams per step", **cpu_info()},
         "e2e": {"value": value, "unit": "seams/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -536,9 +747,13 @@ def run_native(a):
     from paper_2410_21207_gb300 import binding as sc
 
     ws, rank, local = _dist()
-    serving_imgs = None
-    if rank == 0 and not a.no_serving:
-        serving_imgs = pregenerate_serving(a.serving_requests)   # before any GPU work (spawned pool)
+    serving_imgs, canvases, sample5 = None, [], {}
+    if rank == 0:
+        # pixels made before any GPU work (a spawned pool)
+        serving_imgs, canvases, sample5 = pregenerate(
+            0 if a.no_serving else a.serving_requests,
+            not a.no_serving and a.trace_requests > 0,
+            cpu_sample_indices() if (not a.no_cpu_baseline and ws == 1) else [])
     if ws > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -600,6 +815,7 @@ def run_native(a):
     dp_bytes_per_launch = dp_bytes / max(seams, 1)
     achieved = (dp_bytes * a.steps) / (dp_ms / 1000.0) / 1e9 if dp_ms > 0 else None
     peak, peak_src = _peaks()
+    l2 = l2_peak(torch, dev)
     traffic = _traffic_from_profile()
 
     line = {
@@ -614,8 +830,8 @@ def run_native(a):
         "gpu_launches": int(launches) * a.steps,
         "roofline": {"kernel": "k_dp (seam search)", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "peak_source": peak_src, "dp_ms_per_launch": dp_ms / max(dp_n, 1),
-                     "algorithmic_bytes_per_launch": dp_bytes_per_launch},
+                     "peak_source": peak_src, "l2_peak": l2, "l2_frac": (achieved / l2) if achieved else None,
+                     "dp_ms_per_launch": dp_ms / max(dp_n, 1), "algorithmic_bytes_per_launch": dp_bytes_per_launch},
         "clocks": clk.summary(),
     }
 
@@ -631,20 +847,23 @@ def run_native(a):
         line["e2e"] = {"value": seams / e2e_s, "unit": "seams/s", "h2d_bytes_per_step": H * W * 3,
                        "d2h_bytes_per_step": th * tw * 3}
     if rank == 0 and not a.no_batched:
-        line["batched"] = batched_measurement(sc, torch, dev, flush, a.steps)
+        line["batched"] = batched_measurement(sc, torch, dev, flush, a.steps, peak, l2)
     if rank == 0 and not a.no_4k:
         line["uhd_3840x2160"] = fourk_measurement(sc, torch, dev, flush, a.steps)
-    if rank == 0 and not a.no_4k:
-        line["uhd_search_concurrent"] = uhd_search_measurement(sc, torch, dev, a.steps, peak)
+        line["uhd_search_concurrent"] = uhd_search_measurement(sc, torch, dev, a.steps, peak, l2)
     if rank == 0 and not a.no_paper:
         line["enlarge_1920x1080"] = enlarge_measurement(sc, torch, dev, img)
         line["forward_energy_1920x1080"] = forward_measurement(sc, torch, dev, img, tw, th, seams)
         line["paper_nxn"] = paper_workload_measurement(sc, torch, dev, cpu=not a.no_cpu_baseline and ws == 1)
-    if rank == 0 and serving_imgs is not None:
+    if rank == 0 and serving_imgs:
         line["serving"] = serving_measurement(sc, torch, dev, serving_imgs, a.serving_requests)
+    if rank == 0 and canvases:
+        line["serving_trace"] = trace_replay_measurement(sc, torch, dev, canvases, a.trace_requests)
     if rank == 0 and not a.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(job, img_np)
+        line["cpu_oracle"] = cpu_oracle_configs(sample5)
     if rank == 0:
+        line["summary"] = summary(line)
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -653,10 +872,81 @@ def run_native(a):
     return 0
 
 
+def summary(line):
+    """The headline figures of every workload in a few hundred bytes (the line's last key, so
+    that a reader who keeps only the end of the output still has them)."""
+    def r(x, nd=3):
+        return None if x is None else round(float(x), nd)
+    out = {"c2_seams_s": r(line["value"], 0), "k_dp_us": r(1e3 * line["roofline"]["dp_ms_per_launch"], 1),
+           "k_dp_hbm_frac": r(line["roofline"]["frac"], 4), "k_dp_l2_frac": r(line["roofline"]["l2_frac"], 4),
+           "l2_peak_gbs": r(line["roofline"]["l2_peak"], 0)}
+    if "e2e" in line:
+        out["c2_e2e_seams_s"] = r(line["e2e"]["value"], 0)
+    if "uhd_3840x2160" in line:
+        out["c3_seams_s"] = r(line["uhd_3840x2160"]["seams_per_s"], 0)
+    if "uhd_search_concurrent" in line:
+        u = line["uhd_search_concurrent"]
+        out["uhd_maps"] = u["maps"]
+        out["uhd_kernel_us"] = r(u["kernel_us_per_launch"], 1)
+        out["uhd_call_us"] = r(u["us_per_call"], 1)
+        out["uhd_hbm_frac"] = r(u["frac"])
+        out["uhd_l2_frac"] = r(u["l2_frac"])
+        out["uhd_call_hbm_frac"] = r(u["call_frac"])
+    if "batched" in line:
+        b = line["batched"]
+        out["c4_seams_s"] = r(b["seams_per_s"], 0)
+        out["c4_over_plain"] = r(b["batched_over_plain"], 2)
+        out["k_batch_hbm_frac"] = r(b["roofline"]["frac"])
+        out["k_batch_l2_frac"] = r(b["roofline"]["l2_frac"])
+    if "serving" in line:
+        sv = line["serving"]
+        out["c5_300_p50_ms"] = r(sv["served"]["p50_ms"], 1)
+        out["c5_300_p99_ms"] = r(sv["served"]["p99_ms"], 1)
+        out["c5_capacity_over_plain"] = r(sv["served_over_plain_throughput"], 2)
+    if "serving_trace" in line:
+        t = line["serving_trace"]
+        out["c5_full_requests"] = t["requests"]
+        out["c5_full_p50_ms"] = r(t["p50_ms"], 1)
+        out["c5_full_p99_ms"] = r(t["p99_ms"], 1)
+        out["c5_full_req_s"] = r(t["req_per_s"], 1)
+    if "forward_energy_1920x1080" in line:
+        out["fwd_c2_seams_s"] = r(line["forward_energy_1920x1080"]["seams_per_s"], 0)
+    if "cpu_oracle" in line:
+        c = line["cpu_oracle"]
+        out["cpu"] = {"cores": c["host_cores"], "model": c["cpu_model"],
+                      "c2_seams_s": r(line["cpu_baseline"]["value"], 1),
+                      "c3_seams_s": r(c["config3"]["seams_per_s"], 1),
+                      "c4_seams_s": r(c["config4"]["seams_per_s"], 1)}
+        if "config5" in c:
+            out["cpu"]["c5_req_s"] = r(c["config5"]["req_per_s"], 2)
+    return out
+
+
+def profile_batch(n: int):
+    """The first n images of the batched workload through a batch plan (no autotuning), run twice
+    (the kernel to capture is k_batch)."""
+    import torch
+    from paper_2410_21207_gb300 import binding as sc
+    from paper_2410_21207_gb300 import synth
+    jobs = synth.config4()[:n]
+    imgs = [torch.from_numpy(j.make()).to("cuda:0") for j in jobs]
+    plan = sc.BatchPlan(imgs, [(j.target_w, j.target_h) for j in jobs])
+    for _ in range(2):
+        plan.run()
+    torch.cuda.synchronize()
+    sc.check()
+    info = plan.info()
+    plan.close()
+    print(json.dumps({"profile_batch": n, "plan": info, "ok": True}))
+    return 0
+
+
 def main():
     a = _args()
     if a.profile_search:
         return profile_search(a.profile_search)
+    if a.profile_batch:
+        return profile_batch(a.profile_batch)
     if a.impl == "reference":
         return run_reference(a)
     return run_native(a)

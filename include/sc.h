@@ -30,8 +30,8 @@
  *     the stream.
  *   - Return value: SC_OK (0) or a negative sc_status. sc_last_error() describes the last failure
  *     of the calling thread.
- *   - Limits: 1 <= H, W; H <= SC_MAX_ROWS rows for a seam search (cost fits 24 bits with headroom
- *     for C = 4); W <= SC_MAX_COLS; H*W*C < 2^31.
+ *   - Limits: 1 <= H, W; H <= SC_MAX_ROWS; W <= SC_MAX_COLS; H*W*C < 2^31. Seam costs are exact
+ *     for every uint16 energy map of these sizes (they stay below 2^31).
  */
 #ifndef SC_GB300_H
 #define SC_GB300_H
@@ -62,8 +62,10 @@ int sc_version(void);
 /* Message for the last failing call on this thread (static storage, never NULL). */
 const char *sc_last_error(void);
 
-/* Wait for `stream` and report device-side errors recorded by earlier calls on it (and clear
- * them). Returns SC_OK, SC_EINTERNAL, SC_ETIMEOUT or SC_ECUDA. */
+/* Wait for `stream` and report device-side errors recorded by earlier calls on it, by batched
+ * launches on the current device, and by sc_find_seam_static calls on the current device whose work
+ * has finished (and clear them). Returns SC_OK, SC_ETIMEOUT (a bounded wait ran out; takes
+ * precedence), SC_EINTERNAL (a consistency check failed) or SC_ECUDA. */
 int sc_check(void *stream);
 
 /* Free every workspace the library holds for the current device (after synchronising it). */
@@ -88,12 +90,15 @@ int sc_energy(const uint8_t *img, int H, int W, int C, uint16_t *energy_out, voi
 
 /* ---- one minimum vertical seam (section "DP Seam Carving", Algorithm 3, with the readings in
  * the header comment) ----
- * energy:   device, H x W uint16, row-major (any values; the sum along a seam must stay below
- *           2^24, which H <= SC_MAX_ROWS guarantees for energies <= 2040).
+ * energy:   device, H x W uint16, row-major; any values.
  * seam_out: device, int32[H]; seam_out[i] in [0, W), |seam_out[i] - seam_out[i-1]| <= 1.
  * cost_out: device, int64[1] or NULL: the seam's total energy (the minimum of M's last row).
- * Errors: SC_EINVAL for NULL energy/seam_out, H < 1, W < 1, H > SC_MAX_ROWS, W > SC_MAX_COLS,
- *         or energies that could overflow (checked on the device: SC_EINTERNAL via sc_check). */
+ * The fast search packs each cost with its backtrack ancestor into 32 bits, which holds costs
+ * below 2^24; while copying the map the library checks H * max(e) < 2^24 on the device, and a map
+ * that fails it is searched instead by a slower kernel with exact 32-bit costs (one CTA, about
+ * 0.1 ms per 1080 x 1920 map). Both give the same seam and cost; nothing is refused.
+ * Errors: SC_EINVAL for NULL energy/seam_out, H < 1, W < 1, H > SC_MAX_ROWS, W > SC_MAX_COLS;
+ *         device-side check failures via sc_check. */
 int sc_find_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_t *cost_out, void *stream);
 
 /* ---- forward energy (the paper cites it as an alternative to e1 without a formula) ----
@@ -105,7 +110,8 @@ int sc_find_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_
  * leftmost ties, leftmost last-row minimum.
  * sc_forward_costs: the three uint16 H x W planes of a device image (C in {1,3,4}).
  * sc_find_seam_forward: the seam of caller planes (device uint16 H x W each; DL/DR entries with no
- *   predecessor are ignored); W <= 4096; range check as sc_find_seam on CU + max(DL, DR).
+ *   predecessor are ignored); W <= 4096; any values (a map whose H * max(CU + max(DL, DR)) could
+ *   reach 2^24 goes to the exact wide-cost search, as in sc_find_seam).
  * sc_carve_forward: sc_carve with forward energy (same arguments, seam and cost logs); every
  *   searched width (W, and H when target_h < H) must be <= 4096.
  * All asynchronous on `stream`. Errors: SC_EINVAL for null pointers or shapes out of range; device
@@ -150,7 +156,8 @@ int sc_greedy_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int6
  * seams_out: device int32[n*H] (map k's seam at seams_out + k*H); costs_out: device int64[n] or
  * NULL. One thread-block cluster per map; the clusters share the GPU, so with several maps in
  * flight the pass is bound by memory bandwidth rather than by one map's chain of dependent rows.
- * Results equal n calls of sc_find_seam. Errors: as sc_find_seam; n < 1 -> SC_EINVAL. */
+ * Results equal n calls of sc_find_seam (each map's energy range is checked on its own; maps that
+ * fail it go to the wide-cost search). Errors: as sc_find_seam; n < 1 -> SC_EINVAL. */
 int sc_find_seam_multi(const uint16_t *const *energies, int n, int H, int W, int32_t *seams_out, int64_t *costs_out,
                        void *stream);
 
@@ -166,21 +173,33 @@ int sc_find_seam_multi_shape(int warps, int tile_rows);
  * For programs that must not let a library allocate device memory: cudaMalloc/cudaFree can
  * synchronise the device and take unpredictable time inside a latency-critical loop, and hosts
  * that budget every device byte through their own allocator forbid allocations they do not
- * control. Same arguments, result and limits as sc_find_seam, but every scratch byte (a padded
- * copy of the energy map, the saved cost rows, two status words) lives in one fixed array of
- * 32 MiB inside the library's device image, held by every GPU that loads the library until the
- * process exits; the call never calls cudaMalloc or cudaFree.
- *   - Size limit: the map must fit the array, roughly H * (W + 1280) * 2 bytes plus one row of
- *     4-byte costs per 32 rows (3840 x 2160 fits). Larger maps return SC_EINVAL (a message naming
- *     the bytes needed goes to stderr), before any work is enqueued.
+ * control. Same arguments and result as sc_find_seam (any uint16 map, exact seam and cost), but
+ * every scratch byte (a padded copy of the energy map, the saved cost rows, the wide-cost search's
+ * directions and ancestors, three status words) lives in one fixed array of 32 MiB inside the
+ * library's device image, held by every GPU that loads the library until the process exits; the
+ * call never calls cudaMalloc or cudaFree. Differences from sc_find_seam:
+ *   - Size limit: the map must fit the array, roughly H * (W + 1280) * 2.3 bytes plus one row of
+ *     4-byte costs per 32 rows (3840 x 2160 fits). A larger map returns SC_EINVAL (sc_last_error
+ *     names the bytes needed) before any work is enqueued.
+ *   - Device-side errors (a bounded wait that ran out, a failed self-check) are reported twice:
+ *     through the outputs (every seam_out entry, and *cost_out when given, set to -1) and by the
+ *     next sc_check on any stream of the device once the call's work has finished.
  *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress);
  *     make that first call before any stream capture.
  *   - All calls share the one array, which keeps the previous call's contents: calls whose work
  *     overlaps on the GPU (different streams, or different host threads) race and must be
- *     serialised by the caller. The status words are cleared by each call.
- *   - If H * max(energy) could reach 2^24, the search is skipped and every entry of seam_out (and
- *     *cost_out when given) is set to -1. Argument errors: as sc_find_seam. */
+ *     serialised by the caller. Each call clears its own status words first.
+ * Argument errors: SC_EINVAL as sc_find_seam; a failed CUDA call returns SC_ECUDA. */
 int sc_find_seam_static(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_t *cost_out, void *stream);
+
+/* Failure-detection self-test of sc_find_seam_static's error path (no counterpart in the paper).
+ * Enqueues what a static call does when its device work fails, without a fault: it clears the
+ * call's status words, runs the bounded mbarrier wait of the seam search on a barrier that nothing
+ * completes (recording a timeout after limit_us, 1 .. 1e6), then the completion step of every
+ * static call, which sets seam_out[0 .. H) and *cost_out (when given) to -1 and leaves the timeout
+ * for the next sc_check (SC_ETIMEOUT). Errors: SC_EINVAL for a limit or H out of range or a null
+ * seam_out. */
+int sc_find_seam_static_selftest(int limit_us, int H, int32_t *seam_out, int64_t *cost_out, void *stream);
 
 /* ---- carve: remove (W - target_w) vertical seams, then (H - target_h) horizontal seams (found
  * as vertical seams of the transposed image), recomputing the energy where the removal changed

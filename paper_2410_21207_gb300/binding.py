@@ -62,6 +62,7 @@ def load(path: Optional[str] = None):
                 "sc_energy": ([P, I, I, I, P, P], I),
                 "sc_find_seam": ([P, I, I, P, P, P], I),
                 "sc_find_seam_static": ([P, I, I, P, P, P], I),
+                "sc_find_seam_static_selftest": ([I, I, P, P, P], I),
                 "sc_find_seam_multi": ([P, I, I, I, P, P, P], I),
                 "sc_greedy_seam": ([P, I, I, P, P, P], I),
                 "sc_enlarge": ([P, I, I, I, I, P, P, P], I),
@@ -275,9 +276,18 @@ def find_seam_static(e):
     H, W = e.shape
     seam = torch.empty(H, dtype=torch.int32, device=e.device)
     cost = torch.empty(1, dtype=torch.int64, device=e.device)
-    code = load().sc_find_seam_static(_ptr(e), H, W, _ptr(seam), _ptr(cost), _stream(torch, e.device))
-    if code != SC_OK:
-        raise ScError(code, "sc_find_seam_static rejected its arguments")
+    _raise(load().sc_find_seam_static(_ptr(e), H, W, _ptr(seam), _ptr(cost), _stream(torch, e.device)))
+    return seam, cost
+
+
+def find_seam_static_selftest(H: int, limit_us: int = 1000, device=None):
+    """sc_find_seam_static_selftest: the static search's device-error path without a fault (a
+    bounded wait that runs out). Returns the (int32[H] seam, int64[1] cost) outputs it wrote."""
+    torch = _torch()
+    dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+    seam = torch.zeros(H, dtype=torch.int32, device=dev)
+    cost = torch.zeros(1, dtype=torch.int64, device=dev)
+    _raise(load().sc_find_seam_static_selftest(int(limit_us), int(H), _ptr(seam), _ptr(cost), _stream(torch, dev)))
     return seam, cost
 
 

@@ -105,6 +105,9 @@ struct Workspace {
   DevBuf<int16_t> lists;          // two generations of pending-removal lists
   DevBuf<uint8_t> hin, hout;     // staging for the host-pointer entry point
   DevBuf<int> flags;             // [0] error word, [1] energy-range gate
+  DevBuf<int> gates;             // one energy-range gate per map of sc_find_seam_multi
+  DevBuf<uint32_t> wdirs;        // wide-cost search: directions and ancestors (per map)
+  DevBuf<uint16_t> wanc;
   DevBuf<uint16_t> Emulti;       // padded maps of sc_find_seam_multi
   DevBuf<int32_t> enl_log;       // sc_enlarge: the k seams, the carved copy, the widening bitmap
   DevBuf<uint8_t> enl_tmp;
@@ -115,7 +118,7 @@ struct Workspace {
   void release_all() {
     img.release(); img2.release(); Mrow.release();
     E.release(); seam.release(); lists.release(); hin.release(); hout.release(); flags.release();
-    Emulti.release(); Mmulti.release(); dargs.release();
+    Emulti.release(); Mmulti.release(); dargs.release(); gates.release(); wdirs.release(); wanc.release();
     enl_log.release(); enl_tmp.release(); enl_bits.release();
     flags_zeroed = false;
   }
@@ -202,6 +205,15 @@ static int launch_search(Workspace &ws, uint16_t *Ebase, int pe, int H, int W, i
   a.err = ws.flags.p;
   a.gate = gate;
   SC_CUDA(timed("dp", st, [&] { return launch_dp(a, st); }));
+  // a map whose seam sums may not fit the 24-bit search was skipped by it (gate set): the wide-cost
+  // search takes it; for every other map this launch returns at once
+  SC_CUDA(timed("dp_wide", st, [&] { return launch_dp_wide(a, ws.wdirs.p, ws.wanc.p, st); }));
+  return SC_OK;
+}
+
+static int ensure_wide(Workspace &ws, int H, int W, int n) {
+  SC_CUDA(ws.wdirs.ensure(wide_dirs_words(H, W) * n));
+  SC_CUDA(ws.wanc.ensure(wide_anc_elems(H, W) * n));
   return SC_OK;
 }
 
@@ -321,8 +333,10 @@ int sc_check(void *stream) {
     if (g) SC_CUDA(cudaMemset(ge, 0, sizeof(int)));
     e |= g;
   }
+  int sbits = 0;
+  if ((rc = static_pending_errors(&sbits))) return rc;
+  e |= sbits;
   if (e & ERR_TIMEOUT) return fail(SC_ETIMEOUT, "a bounded device wait ran out (error word 0x%x)", e);
-  if (e & ERR_ENERGY_RANGE) return fail(SC_EINVAL, "energies too large: a seam sum could reach 2^24");
   if (e) return fail(SC_EINTERNAL, "device consistency check failed (error word 0x%x)", e);
   return SC_OK;
 }
@@ -412,8 +426,9 @@ int sc_find_seam(const uint16_t *energy, int H, int W, int32_t *seam_out, int64_
   const int pe = pitch_e_for(W);
   SC_CUDA(ws.E.ensure((size_t)H * pe));
   SC_CUDA(ws.Mrow.ensure((size_t)((H + KS - 1) / KS + 1) * pe));
+  if ((rc = ensure_wide(ws, H, W, 1))) return rc;
   SC_CUDA(cudaMemsetAsync(ws.flags.p + 1, 0, sizeof(int), st));
-  SC_CUDA(launch_copy_energy(energy, H, W, ws.E.p + E_PADL, pe, ws.flags.p, ws.flags.p + 1, st));
+  SC_CUDA(launch_copy_energy(energy, H, W, ws.E.p + E_PADL, pe, ws.flags.p + 1, st));
   return launch_search(ws, ws.E.p, pe, H, W, seam_out, nullptr, cost_out, ws.flags.p + 1, st);
 }
 
@@ -436,11 +451,13 @@ int sc_find_seam_multi(const uint16_t *const *energies, int n, int H, int W, int
   SC_CUDA(ws.Emulti.ensure(e_per * n));
   SC_CUDA(ws.Mmulti.ensure(m_per * n));
   SC_CUDA(ws.dargs.ensure((size_t)n));
-  SC_CUDA(cudaMemsetAsync(ws.flags.p + 1, 0, sizeof(int), st));
+  SC_CUDA(ws.gates.ensure((size_t)n));
+  if ((rc = ensure_wide(ws, H, W, n))) return rc;
+  SC_CUDA(cudaMemsetAsync(ws.gates.p, 0, (size_t)n * sizeof(int), st));
   std::vector<DpArgs> h(n);
   for (int k = 0; k < n; ++k) {
     uint16_t *Ek = ws.Emulti.p + e_per * k;
-    SC_CUDA(launch_copy_energy(energies[k], H, W, Ek + E_PADL, pe, ws.flags.p, ws.flags.p + 1, st));
+    SC_CUDA(launch_copy_energy(energies[k], H, W, Ek + E_PADL, pe, ws.gates.p + k, st));
     DpArgs &a = h[k];
     a.E = Ek + E_PADL;
     a.pitch_e = pe;
@@ -451,10 +468,12 @@ int sc_find_seam_multi(const uint16_t *const *energies, int n, int H, int W, int
     a.seam_log = nullptr;
     a.cost = costs_out ? costs_out + k : nullptr;
     a.err = ws.flags.p;
-    a.gate = ws.flags.p + 1;
+    a.gate = ws.gates.p + k;
   }
   SC_CUDA(cudaMemcpyAsync(ws.dargs.p, h.data(), n * sizeof(DpArgs), cudaMemcpyHostToDevice, st));
   SC_CUDA(timed("dp_multi", st, [&] { return launch_dp_multi(ws.dargs.p, n, H, W, st); }));
+  // maps whose seam sums may not fit 24 bits (their gates set) were skipped above
+  SC_CUDA(timed("dp_wide", st, [&] { return launch_dp_wide_multi(ws.dargs.p, n, H, W, ws.wdirs.p, ws.wanc.p, st); }));
   return SC_OK;
 }
 
@@ -509,8 +528,9 @@ int sc_find_seam_forward(const uint16_t *cu, const uint16_t *dl, const uint16_t 
   const int64_t pstride = (int64_t)H * pe;
   SC_CUDA(ws.E.ensure((size_t)3 * H * pe));
   SC_CUDA(ws.Mrow.ensure((size_t)((H + KS - 1) / KS + 1) * pe));
+  if ((rc = ensure_wide(ws, H, W, 1))) return rc;
   SC_CUDA(cudaMemsetAsync(ws.flags.p + 1, 0, sizeof(int), st));
-  SC_CUDA(launch_copy_planes(cu, dl, dr, H, W, ws.E.p + E_PADL, pe, pstride, ws.flags.p, ws.flags.p + 1, st));
+  SC_CUDA(launch_copy_planes(cu, dl, dr, H, W, ws.E.p + E_PADL, pe, pstride, ws.flags.p + 1, st));
   return launch_search(ws, ws.E.p, pe, H, W, seam_out, nullptr, cost_out, ws.flags.p + 1, st, pstride);
 }
 

@@ -17,6 +17,9 @@ int check_carve_args(const void *img, int H, int W, int C, int tw, int th, const
 int carve_impl(const uint8_t *img, int H, int W, int C, int tw, int th, uint8_t *out, int32_t *seam_log,
                int64_t *cost_log, cudaStream_t st, bool forward = false);
 int *device_error_word();
+// errors recorded by sc_find_seam_static calls on the current device and not yet reported (read and
+// cleared; 0 when no static call ran on the device)
+int static_pending_errors(int *bits);
 
 struct BatchCfg {
   int nw, kt;

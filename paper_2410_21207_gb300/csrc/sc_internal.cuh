@@ -33,7 +33,7 @@ constexpr int MAX_CLUSTER = 16;
 // Error bits recorded on the device.
 constexpr int ERR_FILL_MISMATCH = 1;   // backtrack fill disagrees with the ancestor chain
 constexpr int ERR_COST_MISMATCH = 2;   // recomputed cost disagrees with the argmin
-constexpr int ERR_ENERGY_RANGE = 4;    // energies too large for the 24-bit cost field
+constexpr int ERR_ENERGY_RANGE = 4;    // gate bit: seam sums may not fit the 24-bit cost field (not an error)
 constexpr int ERR_TIMEOUT = 8;         // a bounded wait ran out
 constexpr int ERR_BAD_SEAM = 16;       // a seam column out of range
 
@@ -57,7 +57,8 @@ struct DpArgs {
   int32_t *seam_log;   // nullable, out [H]
   int64_t *cost;       // nullable, out [1]
   int *err;            // device error word
-  const int *gate;     // nullable: if *gate != 0 the search is skipped (energy range failure)
+  const int *gate;     // nullable: with ERR_ENERGY_RANGE set the 24-bit search skips the map and the
+                       // wide-cost search takes it
   int64_t pstride = 0; // forward energy: elements between the CU, DL, DR planes (0: the e1 map)
 };
 
@@ -68,19 +69,28 @@ cudaError_t launch_unpack(const uint32_t *img, int pitch_img, int H, int W, int 
 cudaError_t launch_transpose(const uint32_t *src, int pitch_src, int H, int W, uint32_t *dst, int pitch_dst,
                              cudaStream_t st);
 cudaError_t launch_energy(const uint32_t *img, int pitch_img, int H, int W, uint16_t *E, int pitch_e, cudaStream_t st);
-cudaError_t launch_copy_energy(const uint16_t *src, int H, int W, uint16_t *E, int pitch_e, int *err, int *gate,
-                               cudaStream_t st);
+// caller map -> padded layout; sets *gate (ERR_ENERGY_RANGE) when a seam sum might not fit 24 bits
+cudaError_t launch_copy_energy(const uint16_t *src, int H, int W, uint16_t *E, int pitch_e, int *gate, cudaStream_t st);
 cudaError_t launch_unpad_energy(const uint16_t *E, int pitch_e, int H, int W, uint16_t *dst, cudaStream_t st);
 // forward energy: the CU, DL, DR planes of a word image, or of a caller's planes (with the range
-// check and the unused border entries zeroed), plane p at E + p * pstride
+// gate and the unused border entries zeroed), plane p at E + p * pstride
 cudaError_t launch_forward(const uint32_t *img, int pitch, int H, int W, uint16_t *E, int pitch_e, int64_t pstride,
                            cudaStream_t st);
 cudaError_t launch_copy_planes(const uint16_t *cu, const uint16_t *dl, const uint16_t *dr, int H, int W, uint16_t *E,
-                               int pitch_e, int64_t pstride, int *err, int *gate, cudaStream_t st);
+                               int pitch_e, int64_t pstride, int *gate, cudaStream_t st);
 cudaError_t launch_refresh_fwd(const uint32_t *img, int pitch, uint16_t *E, int pe, int64_t pstride, int H, int W,
                                const int32_t *seam, const int16_t *lists_in, int16_t *lists_out, int m, int *err,
                                cudaStream_t st);
 cudaError_t launch_dp(const DpArgs &a, cudaStream_t st);   // forward energy when a.pstride > 0
+// The wide-cost search (sc_dp_wide.cu): one CTA per map, exact 32-bit costs, for the maps whose
+// gate is set (it returns at once for the others). Scratch per map: wide_dirs_words(H, W) uint32
+// direction words and wide_anc_elems(H, W) uint16 ancestors. Forward energy when a.pstride > 0
+// (W <= 4096); the multi-map form takes a device array of n DpArgs of one size (e1 only).
+cudaError_t launch_dp_wide(const DpArgs &a, uint32_t *dirs, uint16_t *anc, cudaStream_t st);
+cudaError_t launch_dp_wide_multi(const DpArgs *dargs_dev, int n, int H, int W, uint32_t *dirs, uint16_t *anc,
+                                 cudaStream_t st);
+size_t wide_dirs_words(int H, int W);
+size_t wide_anc_elems(int H, int W);
 int dp_forward_max_width();                                 // widest map the forward search takes
 // n searches of H x W maps in one launch (one cluster each); dargs_dev is a device array
 cudaError_t launch_dp_multi(const DpArgs *dargs_dev, int n, int H, int W, cudaStream_t st);

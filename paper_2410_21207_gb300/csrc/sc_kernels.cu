@@ -65,39 +65,41 @@ __global__ void k_forward(const uint32_t *__restrict__ img, int pitch, int H, in
 }
 
 // ---- caller forward planes -> padded layout. DL in row 0 and column 0 and DR in row 0 and the
-// last column are never used (no such predecessor) and are stored as 0; the range check bounds
-// every cell's CU + max(DL, DR). ----
+// last column are never used (no such predecessor) and are stored as 0. A cell whose
+// CU + max(DL, DR) exceeds `limit` sets the map's gate: its seam sums may not fit the 24-bit cost
+// field, and the wide-cost search takes the map (one atomic per warp). ----
 __global__ void k_copy_planes(const uint16_t *__restrict__ cu, const uint16_t *__restrict__ dl,
                               const uint16_t *__restrict__ dr, int H, int W, uint16_t *__restrict__ E, int pe,
-                              int64_t pstride, uint32_t limit, int *err, int *gate) {
+                              int64_t pstride, uint32_t limit, int *gate) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y;
-  if (j >= W || i >= H) return;
-  const int64_t q = (int64_t)i * W + j;
-  const uint32_t u = cu[q];
-  const uint32_t l = (i >= 1 && j >= 1) ? dl[q] : 0u;
-  const uint32_t r = (i >= 1 && j + 1 < W) ? dr[q] : 0u;
-  E[(int64_t)i * pe + j] = (uint16_t)u;
-  E[pstride + (int64_t)i * pe + j] = (uint16_t)l;
-  E[2 * pstride + (int64_t)i * pe + j] = (uint16_t)r;
-  if (u + (l > r ? l : r) > limit) {
-    atomicOr(err, ERR_ENERGY_RANGE);
-    atomicOr(gate, ERR_ENERGY_RANGE);
+  bool over = false;
+  if (j < W && i < H) {
+    const int64_t q = (int64_t)i * W + j;
+    const uint32_t u = cu[q];
+    const uint32_t l = (i >= 1 && j >= 1) ? dl[q] : 0u;
+    const uint32_t r = (i >= 1 && j + 1 < W) ? dr[q] : 0u;
+    E[(int64_t)i * pe + j] = (uint16_t)u;
+    E[pstride + (int64_t)i * pe + j] = (uint16_t)l;
+    E[2 * pstride + (int64_t)i * pe + j] = (uint16_t)r;
+    over = u + (l > r ? l : r) > limit;
   }
+  if (__any_sync(0xffffffffu, over) && (threadIdx.x & 31) == 0) atomicOr(gate, ERR_ENERGY_RANGE);
 }
 
-// ---- caller energy -> padded layout, with the range check of the 24-bit cost field ----
+// ---- caller energy -> padded layout; an energy above `limit` sets the map's gate (its seam sums
+// may not fit the 24-bit cost field: the wide-cost search takes the map; one atomic per warp) ----
 __global__ void k_copy_energy(const uint16_t *__restrict__ src, int H, int W, uint16_t *__restrict__ E, int pe,
-                              uint32_t limit, int *err, int *gate) {
+                              uint32_t limit, int *gate) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y;
-  if (j >= W || i >= H) return;
-  const uint16_t v = src[(int64_t)i * W + j];
-  E[(int64_t)i * pe + j] = v;
-  if (v > limit) {
-    atomicOr(err, ERR_ENERGY_RANGE);
-    atomicOr(gate, ERR_ENERGY_RANGE);
+  bool over = false;
+  if (j < W && i < H) {
+    const uint16_t v = src[(int64_t)i * W + j];
+    E[(int64_t)i * pe + j] = v;
+    over = v > limit;
   }
+  if (__any_sync(0xffffffffu, over) && (threadIdx.x & 31) == 0) atomicOr(gate, ERR_ENERGY_RANGE);
 }
 
 __global__ void k_unpad_energy(const uint16_t *__restrict__ E, int pe, int H, int W, uint16_t *__restrict__ dst) {
@@ -191,12 +193,11 @@ cudaError_t launch_energy(const uint32_t *img, int pitch, int H, int W, uint16_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_copy_energy(const uint16_t *src, int H, int W, uint16_t *E, int pe, int *err, int *gate,
-                               cudaStream_t st) {
-  // the seam search keeps costs in 24 bits: every seam sum must stay below 2^24
+cudaError_t launch_copy_energy(const uint16_t *src, int H, int W, uint16_t *E, int pe, int *gate, cudaStream_t st) {
+  // the 24-bit search keeps costs below 2^24: every seam sum must fit
   const uint32_t limit = (uint32_t)((((uint64_t)1 << 24) - 1) / (uint64_t)H);
   dim3 grid((W + 127) / 128, H);
-  k_copy_energy<<<grid, 128, 0, st>>>(src, H, W, E, pe, limit, err, gate);
+  k_copy_energy<<<grid, 128, 0, st>>>(src, H, W, E, pe, limit, gate);
   return cudaGetLastError();
 }
 
@@ -208,10 +209,10 @@ cudaError_t launch_forward(const uint32_t *img, int pitch, int H, int W, uint16_
 }
 
 cudaError_t launch_copy_planes(const uint16_t *cu, const uint16_t *dl, const uint16_t *dr, int H, int W, uint16_t *E,
-                               int pe, int64_t pstride, int *err, int *gate, cudaStream_t st) {
+                               int pe, int64_t pstride, int *gate, cudaStream_t st) {
   const uint32_t limit = (uint32_t)((((uint64_t)1 << 24) - 1) / (uint64_t)H);
   dim3 grid((W + 127) / 128, H);
-  k_copy_planes<<<grid, 128, 0, st>>>(cu, dl, dr, H, W, E, pe, pstride, limit, err, gate);
+  k_copy_planes<<<grid, 128, 0, st>>>(cu, dl, dr, H, W, E, pe, pstride, limit, gate);
   return cudaGetLastError();
 }
 

@@ -56,6 +56,13 @@ def test_argument_errors_are_synchronous():
     assert lib.sc_enlarge(P(0), 10, 10, 3, 15, fake, P(0), P(0)) == binding.SC_EINVAL
     assert lib.sc_greedy_seam(P(0), 10, 10, fake, P(0), P(0)) == binding.SC_EINVAL
     assert lib.sc_selftest_wait_timeout(0, P(0)) == binding.SC_EINVAL
+    assert lib.sc_find_seam_static(P(0), 10, 10, fake, P(0), P(0)) == binding.SC_EINVAL
+    assert lib.sc_find_seam_static(fake, 10, binding.MAX_COLS + 1, fake, P(0), P(0)) == binding.SC_EINVAL
+    # a map larger than the static scratch array is refused before any CUDA call, with the bytes named
+    assert lib.sc_find_seam_static(fake, 4000, 4000, fake, P(0), P(0)) == binding.SC_EINVAL
+    assert b"bytes of scratch" in lib.sc_last_error()
+    assert lib.sc_find_seam_static_selftest(0, 10, fake, P(0), P(0)) == binding.SC_EINVAL
+    assert lib.sc_find_seam_static_selftest(1000, 0, fake, P(0), P(0)) == binding.SC_EINVAL
     assert lib.sc_find_seam_multi_shape(5, 8) == binding.SC_EINVAL
     assert lib.sc_find_seam_multi_shape(0, 0) == binding.SC_OK
     maps = (P * 2)(fake, P(0))

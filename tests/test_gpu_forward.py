@@ -50,6 +50,21 @@ def test_find_seam_forward_parity(dev, H, W):
         np.testing.assert_array_equal(seam.cpu().numpy(), s_ref, err_msg=f"{H}x{W} {kind}")
 
 
+@pytest.mark.parametrize("H,W", [(2000, 300), (8192, 40), (1080, 1920)])
+def test_find_seam_forward_wide_costs(dev, H, W):
+    """Caller planes whose seam sums do not fit the 24-bit cost field (H * max(CU + max(DL, DR))
+    >= 2^24) go to the wide-cost search; seam and cost equal the oracle's."""
+    rng = np.random.default_rng(H + W)
+    planes = (rng.integers(30000, 65536, size=(H, W)).astype(np.uint16),
+              rng.integers(0, 65536, size=(H, W)).astype(np.uint16),
+              rng.integers(0, 65536, size=(H, W)).astype(np.uint16))
+    seam, cost = sc.find_seam_forward(*[_t(p, dev) for p in planes])
+    sc.check()
+    s_ref, c_ref = oracle.dp_seam_forward(*planes)
+    assert int(cost.cpu()[0]) == c_ref
+    np.testing.assert_array_equal(seam.cpu().numpy(), s_ref)
+
+
 def test_carve_forward_small_both_passes(dev):
     rng = np.random.default_rng(77)
     for k in range(14):

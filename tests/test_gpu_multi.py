@@ -86,10 +86,16 @@ def test_multi_uhd(dev, shape):
     _check(dev, maps)
 
 
-def test_multi_energy_range_rejected(dev):
-    e = np.full((2000, 16), 60000, dtype=np.uint16)   # 2000 * 60000 >= 2^24
-    sc.find_seam_multi([torch.from_numpy(e).to(dev)] * 2)
-    with pytest.raises(sc.ScError) as ei:
-        sc.check()
-    assert ei.value.code == sc.SC_EINVAL
-    sc.check()
+def test_multi_mixed_energy_ranges(dev):
+    """Maps of one batch on both sides of the 24-bit cost limit: each map's range is checked on its
+    own, the over-range ones go to the wide-cost search, and every seam and cost equals the
+    oracle's."""
+    rng = np.random.default_rng(90)
+    H, W = 1200, 900
+    maps = [rng.integers(0, 1531, size=(H, W)), np.full((H, W), 65535), rng.integers(0, 65536, size=(H, W)),
+            rng.integers(0, 3, size=(H, W)), rng.integers(65530, 65536, size=(H, W)), np.full((H, W), 9)]
+    _check(dev, [m.astype(np.uint16) for m in maps])
+    # the tallest over-range maps, twice in a row (the second call reuses the scratch)
+    for _ in range(2):
+        _check(dev, [np.full((8192, 40), 60000, dtype=np.uint16),
+                     rng.integers(0, 65536, size=(8192, 40)).astype(np.uint16)])

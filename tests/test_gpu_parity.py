@@ -76,13 +76,33 @@ def test_greedy_seam_parity(dev, H, W):
         np.testing.assert_array_equal(_np(seam), s_ref, err_msg=f"{H}x{W} {kind}")
 
 
-def test_find_seam_energy_range_rejected(dev):
-    e = np.full((2000, 16), 60000, dtype=np.uint16)   # 2000 * 60000 >= 2^24
-    sc.find_seam(_to_dev(e, dev))
-    with pytest.raises(sc.ScError) as ei:
-        sc.check()
-    assert ei.value.code == sc.SC_EINVAL
-    sc.check()   # cleared
+@pytest.mark.parametrize("H,W,kind", [
+    (2000, 16, "const60000"),     # 2000 * 60000 >= 2^24: every seam sum beyond the 24-bit field
+    (1080, 1920, "max"),          # every energy 65535: all ties, cost 1080 * 65535
+    (1080, 1920, "uniform"),      # any uint16 value
+    (1080, 1920, "ties"),         # 3 values near the top: many exact ties
+    (8192, 40, "max"),            # the tallest map: cost 8192 * 65535 (2^29)
+    (8192, 40, "uniform"),
+    (257, 8192, "uniform"),       # the widest map
+    (1, 1, "max"), (1, 5, "uniform"), (3, 1, "max"), (17, 63, "ties"), (300, 129, "band"),
+])
+def test_find_seam_wide_costs(dev, H, W, kind):
+    """Maps whose seam sums do not fit the fast search's 24-bit cost field (H * max(e) >= 2^24):
+    they go to the wide-cost search, and the seam and the int64 cost still equal Algorithm 3's
+    (the oracle's, with int64 costs)."""
+    rng = np.random.default_rng(H * 7 + W)
+    e = {"const60000": lambda: np.full((H, W), 60000),
+         "max": lambda: np.full((H, W), 65535),
+         "uniform": lambda: rng.integers(0, 65536, size=(H, W)),
+         "ties": lambda: rng.integers(65533, 65536, size=(H, W)),
+         "band": lambda: rng.integers(60000, 60003, size=(H, W))}[kind]().astype(np.uint16)
+    # most of these exceed the 24-bit field (H * max(e) >= 2^24); the short ones check that large
+    # values that still fit stay on the fast search with the same answer
+    seam, cost = sc.find_seam(_to_dev(e, dev))
+    sc.check()
+    s_ref, c_ref = oracle.dp_seam(e)
+    assert int(_np(cost)[0]) == c_ref
+    np.testing.assert_array_equal(_np(seam), s_ref)
 
 
 @pytest.mark.parametrize("H,W,lo,hi", [

@@ -164,6 +164,45 @@ def test_seam_invariants_and_greedy_bound():
         assert c == last.min() and s[-1] == int(np.argmin(last))
 
 
+def _brute_last_row(e):
+    """For every bottom column j, the minimum energy over all 8-connected top-to-bottom paths that
+    end at (H-1, j), by enumerating the paths (no recurrence)."""
+    H, W = e.shape
+    best = [None] * W
+
+    def walk(i, j, acc):   # extend a path that has reached (i, j) with energy acc
+        acc += int(e[i, j])
+        if i == H - 1:
+            if best[j] is None or acc < best[j]:
+                best[j] = acc
+            return
+        for nj in (j - 1, j, j + 1):
+            if 0 <= nj < W:
+                walk(i + 1, nj, acc)
+
+    for j0 in range(W):
+        walk(0, j0, 0)
+    return np.array(best, dtype=np.int64)
+
+
+def test_dp_last_row_is_the_per_column_path_minimum():
+    """Every entry of M's last row (Algorithm 3's table, not only its minimum) is the least energy
+    of a path ending at that column; this catches a wrong exclusion at either edge or a wrong
+    neighbour at any column, minimal or not."""
+    rng = np.random.default_rng(163)
+    shapes = [(H, W) for H in range(1, 8) for W in range(1, 7)]
+    for H, W in shapes:
+        for kind in range(3):
+            hi = (1531, 3, 65536)[kind]
+            e = rng.integers(0, hi, size=(H, W)).astype(np.uint16)
+            np.testing.assert_array_equal(oracle.dp_last_row(e), _brute_last_row(e), err_msg=f"{H}x{W} {kind}")
+    # edges that must be excluded, not wrapped: a cheap column at the far side of the map would
+    # leak into the first or last column through a wrap-around
+    e = np.array([[9, 9, 9, 0], [9, 9, 9, 9], [9, 9, 9, 9]], dtype=np.uint16)
+    np.testing.assert_array_equal(oracle.dp_last_row(e), _brute_last_row(e))
+    assert list(oracle.dp_last_row(e)) == [27, 18, 18, 18]   # by hand: row 1 is [18, 18, 9, 9]; a wrap would give 18 at column 0
+
+
 def test_closed_forms():
     rng = np.random.default_rng(9)
     # constant image: zero energy, the leftmost straight seam
