@@ -548,7 +548,7 @@ def uhd_search_measurement(sc, torch, dev, steps, peak, l2):
     H, W = 2160, 3840
     B = max(1, sc.find_seam_multi_capacity(H, W))
     e = sc.energy(torch.from_numpy(synth.config3().make()).to(dev))
-    maps = [torch.roll(e, 37 * k, dims=1).contiguous() for k in range(B)]
+    maps = [torch.roll(e.view(torch.int16), 37 * k, dims=1).view(torch.uint16).contiguous() for k in range(B)]
     sc.check()
     for _ in range(3):
         sc.find_seam_multi(maps)

@@ -191,7 +191,7 @@ int workspace_reserve(cudaStream_t st, int H, int W) {
 }
 
 static int launch_search(Workspace &ws, uint16_t *Ebase, int pe, int H, int W, int32_t *seam, int32_t *seam_log,
-                         int64_t *cost, const int *gate, cudaStream_t st, int64_t pstride = 0) {
+                         int64_t *cost, int *gate, cudaStream_t st, int64_t pstride = 0) {
   DpArgs a;
   a.pstride = pstride;
   a.E = Ebase + E_PADL;
@@ -448,22 +448,34 @@ int sc_find_seam_multi(const uint16_t *const *energies, int n, int H, int W, int
   const int pe = pitch_e_for(W);
   const int S = (H + KS - 1) / KS;
   const size_t e_per = (size_t)H * pe, m_per = (size_t)(S + 1) * pe;
-  SC_CUDA(ws.Emulti.ensure(e_per * n));
+  // a map is read in place when its rows are 16-byte aligned (W a multiple of 8, aligned base);
+  // any other map is first copied into a padded workspace
+  auto in_place = [&](int k) { return (W % 8) == 0 && ((uintptr_t)energies[k] & 15u) == 0; };
+  int ncopy = 0;
+  for (int k = 0; k < n; ++k) ncopy += !in_place(k);
+  if (ncopy) SC_CUDA(ws.Emulti.ensure(e_per * ncopy));
   SC_CUDA(ws.Mmulti.ensure(m_per * n));
   SC_CUDA(ws.dargs.ensure((size_t)n));
   SC_CUDA(ws.gates.ensure((size_t)n));
   if ((rc = ensure_wide(ws, H, W, n))) return rc;
   SC_CUDA(cudaMemsetAsync(ws.gates.p, 0, (size_t)n * sizeof(int), st));
   std::vector<DpArgs> h(n);
+  int c = 0;
   for (int k = 0; k < n; ++k) {
-    uint16_t *Ek = ws.Emulti.p + e_per * k;
-    SC_CUDA(launch_copy_energy(energies[k], H, W, Ek + E_PADL, pe, ws.gates.p + k, st));
     DpArgs &a = h[k];
-    a.E = Ek + E_PADL;
-    a.pitch_e = pe;
+    if (in_place(k)) {
+      a.E = energies[k];
+      a.pitch_e = W;
+    } else {
+      uint16_t *Ek = ws.Emulti.p + e_per * c++;
+      SC_CUDA(launch_copy_energy(energies[k], H, W, Ek + E_PADL, pe, ws.gates.p + k, st));
+      a.E = Ek + E_PADL;
+      a.pitch_e = pe;
+    }
     a.H = H;
     a.W = W;
     a.Mrow = ws.Mmulti.p + m_per * k + E_PADL;
+    a.pitch_m = pe;
     a.seam = seams_out + (size_t)k * H;
     a.seam_log = nullptr;
     a.cost = costs_out ? costs_out + k : nullptr;
@@ -472,7 +484,7 @@ int sc_find_seam_multi(const uint16_t *const *energies, int n, int H, int W, int
   }
   SC_CUDA(cudaMemcpyAsync(ws.dargs.p, h.data(), n * sizeof(DpArgs), cudaMemcpyHostToDevice, st));
   SC_CUDA(timed("dp_multi", st, [&] { return launch_dp_multi(ws.dargs.p, n, H, W, st); }));
-  // maps whose seam sums may not fit 24 bits (their gates set) were skipped above
+  // maps whose seam sums may not fit 24 bits (gates set by the search or the copy) were left over
   SC_CUDA(timed("dp_wide", st, [&] { return launch_dp_wide_multi(ws.dargs.p, n, H, W, ws.wdirs.p, ws.wanc.p, st); }));
   return SC_OK;
 }

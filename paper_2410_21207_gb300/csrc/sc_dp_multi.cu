@@ -1,6 +1,8 @@
 // Many seam searches of one size in one launch: cluster c searches map c. Each search is the
 // cluster-wide seam_search (sc_search.cuh); the clusters run side by side, so with enough maps in
 // flight the pass is bound by the GPU's throughput instead of one map's chain of dependent rows.
+// The maps are read where the caller keeps them (seam_search's in-place form, which also checks
+// each map's cost range), so a call moves no more than the search's own bytes.
 // Four tile shapes are built (compute warps per CTA x DP tile rows). The kernel is bound by the
 // latency of its dependent chains, so the shapes are compiled for as many resident CTAs per SM as
 // registers and shared memory allow (2 of 8 warps, 4 of 4 warps; four backtrack-fill warps keep
@@ -23,7 +25,7 @@ __global__ void __launch_bounds__(Geo<NW, KT, true>::THREADS, NW == 8 ? 2 : 4) k
   const int img = blockIdx.x / cg::this_cluster().num_blocks();
   const DpArgs p = ps[img];
   const int S = (p.H + KS - 1) / KS;
-  search_init<NW, KT, true, MULTI_FILL_WARPS>(smem, S);
+  search_init<NW, KT, true, MULTI_FILL_WARPS, false, KS, true>(smem, S);
   cg::this_cluster().sync();
   SearchArgs a;
   a.E = p.E;
@@ -36,8 +38,10 @@ __global__ void __launch_bounds__(Geo<NW, KT, true>::THREADS, NW == 8 ? 2 : 4) k
   a.cost = p.cost;
   a.err = p.err;
   a.gated = (p.gate != nullptr) && (*p.gate & ERR_ENERGY_RANGE);
+  a.pitch_m = p.pitch_m;
+  a.gate = p.gate;
   SearchState st;
-  seam_search<NW, KT, true, MULTI_FILL_WARPS>(a, smem, S, st);
+  seam_search<NW, KT, true, MULTI_FILL_WARPS, false, KS, true>(a, smem, S, st);
 }
 
 namespace {
@@ -51,7 +55,9 @@ struct MultiShape {
 };
 
 template <int NW, int KT>
-size_t multi_smem(int H) { return search_plan<NW, KT, true, MULTI_FILL_WARPS>((H + KS - 1) / KS).total; }
+size_t multi_smem(int H) {
+  return search_plan<NW, KT, true, MULTI_FILL_WARPS, false, KS, true>((H + KS - 1) / KS).total;
+}
 
 template <int NW, int KT>
 cudaError_t multi_configure() {

@@ -52,14 +52,15 @@ struct DpArgs {
   const uint16_t *E;   // row 0, column 0 (already offset by E_PADL)
   int pitch_e;
   int H, W;
-  uint32_t *Mrow;      // super-tile boundary rows, row s at Mrow + s*pitch_e (offset by E_PADL)
+  uint32_t *Mrow;      // super-tile boundary rows, row s at Mrow + s*pitch_m (offset by E_PADL)
   int32_t *seam;       // out [H]
   int32_t *seam_log;   // nullable, out [H]
   int64_t *cost;       // nullable, out [1]
   int *err;            // device error word
-  const int *gate;     // nullable: with ERR_ENERGY_RANGE set the 24-bit search skips the map and the
-                       // wide-cost search takes it
+  int *gate;           // nullable: with ERR_ENERGY_RANGE set the 24-bit search skips the map and the
+                       // wide-cost search takes it (the multi-map search also sets it itself)
   int64_t pstride = 0; // forward energy: elements between the CU, DL, DR planes (0: the e1 map)
+  int pitch_m = 0;     // row stride of Mrow (0: pitch_e)
 };
 
 // Launchers (enqueue on `st`; return cudaError_t of the launch).
@@ -92,7 +93,10 @@ cudaError_t launch_dp_wide_multi(const DpArgs *dargs_dev, int n, int H, int W, u
 size_t wide_dirs_words(int H, int W);
 size_t wide_anc_elems(int H, int W);
 int dp_forward_max_width();                                 // widest map the forward search takes
-// n searches of H x W maps in one launch (one cluster each); dargs_dev is a device array
+// n searches of H x W maps in one launch (one cluster each); dargs_dev is a device array. The maps
+// are read in place (E = row 0, column 0; pitch_e a multiple of 8; 16-byte aligned rows) and each
+// map's 24-bit cost range is checked in the kernel: a map that fails sets its gate and is left to
+// launch_dp_wide_multi
 cudaError_t launch_dp_multi(const DpArgs *dargs_dev, int n, int H, int W, cudaStream_t st);
 // how many H x W searches of launch_dp_multi are resident on the GPU at once
 cudaError_t dp_multi_capacity(int H, int W, int *n_out);

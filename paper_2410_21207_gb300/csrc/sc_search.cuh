@@ -32,6 +32,11 @@
 //     runs a counted loop), and per-super-tile bookkeeping runs after the tile, on its last row
 //     (the only row of a tile where it can occur, since KSS is a multiple of KT).
 // The result is Algorithm 3's seam exactly (leftmost ties, leftmost last-row minimum).
+// With DIRECT the map is the caller's own H x W array (any row pitch that is a multiple of 8
+// elements, 16-byte aligned rows), read in place: the row copies are clipped to the map's columns,
+// the backtrack's loads outside it are skipped, and the 24-bit cost range is checked here instead
+// of by a copy kernel (a per-row maximum of the staged energies, reduced over the cluster; a map
+// that fails it is left to the wide-cost search through its gate).
 // With FWD (forward energy) the map has three planes, CU, DL and DR, and a cell's cost depends on
 // the direction it is reached from: M(i,j) = CU(i,j) + min(M(i-1,j-1) + DL(i,j), M(i-1,j),
 // M(i-1,j+1) + DR(i,j)). Optimal predecessors still never cross (a crossing pair would need
@@ -69,11 +74,11 @@ struct Geo {
 
 // offsets of the dynamic shared-memory regions used by seam_search
 struct SearchPlan {
-  size_t bnd, hbuf, anc, wmin, cmin, jb, misc, fdir, ring, bars, gat, total;
+  size_t bnd, hbuf, anc, wmin, cmin, jb, misc, emx, fdir, ring, bars, gat, total;
   int gw;   // row stride (bytes) of the gathered ancestor table in rank 0; 0: not gathered
 };
 
-template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false, int KSS = KS>
+template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false, int KSS = KS, bool DIRECT = false>
 __host__ __device__ inline SearchPlan search_plan(int S) {
   using G = Geo<NW, KT, CL, FWM, KSS>;
   SearchPlan p;
@@ -85,6 +90,8 @@ __host__ __device__ inline SearchPlan search_plan(int S) {
   p.cmin = o; o += CL ? (size_t)MAX_CLUSTER * 8 : 8;   // every CTA's minimum, pushed to rank 0
   p.jb = o;   o += (size_t)(S + 1) * 4;  o = (o + 15) & ~(size_t)15;
   p.misc = o; o += 16;
+  p.emx = o;  o += DIRECT ? (size_t)(NW + 1 + MAX_CLUSTER) * 4 : 0;   // energy maxima: per warp, per CTA
+  o = (o + 15) & ~(size_t)15;
   // the backtrack fill's direction rows live in the staging ring, which is idle by then (every
   // staged tile has been consumed before the argmin), unless the ring is the smaller of the two
   const size_t fdir_sz = (size_t)G::FW * KSS * 32 * (G::FV == 4 ? 4 : 2), ring_sz = (size_t)NSLOT * (FWD ? 3 : 1) * KT * G::BW * 2;
@@ -108,10 +115,12 @@ __host__ __device__ inline SearchPlan search_plan(int S) {
 }
 
 struct SearchArgs {
-  const uint16_t *E;   // row 0, column 0 (already offset by E_PADL)
+  const uint16_t *E;   // row 0, column 0 (already offset by E_PADL unless DIRECT)
   int pitch_e;
   int H, W;
-  uint32_t *Mrow;      // super-tile boundary cost rows, row s at Mrow + s*pitch_e (offset by E_PADL)
+  uint32_t *Mrow;      // super-tile boundary cost rows, row s at Mrow + s*pitch_m (offset by E_PADL)
+  int pitch_m = 0;     // row stride of Mrow (0: pitch_e)
+  int *gate = nullptr; // DIRECT: receives ERR_ENERGY_RANGE when the map fails the 24-bit range check
   int32_t *seam;       // out [H]
   int32_t *seam_log;   // nullable, out [H]
   int64_t *cost;       // nullable, out [1]
@@ -204,9 +213,17 @@ __device__ __forceinline__ void dp_row(uint32_t (&k)[V], uint2 ev, const uint32_
   k[0] = n0; k[1] = n1; k[2] = n2; k[3] = n3;
 }
 
+// Running maximum of a lane's energies (two uint16 pairs; columns outside the map masked to 0 by
+// cm in warps that hold such columns) for the DIRECT range check; off the row's dependent chain.
+template <bool CHK, bool MASK>
+__device__ __forceinline__ void emax_acc(uint32_t &acc, uint2 ev, uint2 cm) {
+  if (CHK) acc = __vimax3_u16x2(acc, MASK ? (ev.x & cm.x) : ev.x, MASK ? (ev.y & cm.y) : ev.y);
+}
+
 // KT rows of a full tile from the staged energies er (row stride BW); MASK applies oobm.
-template <int KT, int BW, bool MASK, bool LAT = false>
-__device__ __forceinline__ void dp_rows(uint32_t (&k)[V], const uint16_t *er, const uint32_t (&oobm)[V]) {
+template <int KT, int BW, bool MASK, bool LAT = false, bool CHK = false>
+__device__ __forceinline__ void dp_rows(uint32_t (&k)[V], const uint16_t *er, const uint32_t (&oobm)[V],
+                                        uint32_t &acc, uint2 cm) {
   uint2 a = *reinterpret_cast<const uint2 *>(er);
   uint2 b = *reinterpret_cast<const uint2 *>(er + BW);
 #pragma unroll
@@ -215,14 +232,15 @@ __device__ __forceinline__ void dp_rows(uint32_t (&k)[V], const uint16_t *er, co
     a = b;
     if (r + 2 < KT) b = *reinterpret_cast<const uint2 *>(er + (r + 2) * BW);
     dp_row<MASK, LAT>(k, ev, oobm);
+    emax_acc<CHK, MASK>(acc, ev, cm);
   }
 }
 
 // Rows rb .. n-1 (n <= KT) of a tile: the first tile (rb = 1, row 0 initialises) or a ragged
 // last tile, at the pace of a full tile.
-template <int KT, int BW, bool MASK, bool LAT = false>
+template <int KT, int BW, bool MASK, bool LAT = false, bool CHK = false>
 __device__ __forceinline__ void dp_rows_n(uint32_t (&k)[V], const uint16_t *er, const uint32_t (&oobm)[V], int rb,
-                                          int n) {
+                                          int n, uint32_t &acc, uint2 cm) {
   uint2 a = *reinterpret_cast<const uint2 *>(er + rb * BW);
   uint2 b = a;
   if (rb + 1 < n) b = *reinterpret_cast<const uint2 *>(er + (rb + 1) * BW);
@@ -232,6 +250,7 @@ __device__ __forceinline__ void dp_rows_n(uint32_t (&k)[V], const uint16_t *er, 
     a = b;
     if (r + 2 < n) b = *reinterpret_cast<const uint2 *>(er + (r + 2) * BW);
     dp_row<MASK, LAT>(k, ev, oobm);
+    emax_acc<CHK, MASK>(acc, ev, cm);
   }
 }
 
@@ -278,9 +297,9 @@ __device__ __forceinline__ void dp_rows_n_fwd(uint32_t (&k)[V], const uint16_t *
 
 // Initialise the staging and halo mbarriers (thread 0; the caller then synchronises the CTA, and
 // the cluster when CL).
-template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false, int KSS = KS>
+template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false, int KSS = KS, bool DIRECT = false>
 __device__ inline void search_init(unsigned char *smem, int S) {
-  const SearchPlan plan = search_plan<NW, KT, CL, FWM, FWD, KSS>(S);
+  const SearchPlan plan = search_plan<NW, KT, CL, FWM, FWD, KSS, DIRECT>(S);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + plan.bars);
   uint64_t *empty = full + NSLOT;
   uint64_t *hbar = empty + NSLOT;
@@ -302,8 +321,9 @@ __device__ __forceinline__ void group_sync() {
 
 // The search. Every thread of the CTA (of every CTA of the cluster when CL) calls it with the same
 // arguments; `Smax` is the super-tile count the shared-memory plan was sized for.
-template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false, int KSS = KS>
+template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false, int KSS = KS, bool DIRECT = false>
 __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, SearchState &st) {
+  static_assert(!DIRECT || (CL && !FWD), "the in-place form is built for the cluster search of e1 maps");
   constexpr int NP = FWD ? 3 : 1;   // cost planes staged per row
   // the single-map search: one cluster, a CTA per SM, every compute warp alone on its SM
   // sub-partition with 4 warps (latency-bound)
@@ -316,7 +336,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   const bool producer = (warp == NW);
   const int H = p.H, W = p.W;
   const int S = (H + KSS - 1) / KSS;
-  const SearchPlan plan = search_plan<NW, KT, CL, FWM, FWD, KSS>(Smax);
+  const SearchPlan plan = search_plan<NW, KT, CL, FWM, FWD, KSS, DIRECT>(Smax);
   uint32_t *bnd = reinterpret_cast<uint32_t *>(smem + plan.bnd);
   uint32_t *hbuf = reinterpret_cast<uint32_t *>(smem + plan.hbuf);
   uint8_t *ancT = reinterpret_cast<uint8_t *>(smem + plan.anc);
@@ -324,6 +344,7 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   unsigned long long *cmin = reinterpret_cast<unsigned long long *>(smem + plan.cmin);
   int *jb = reinterpret_cast<int *>(smem + plan.jb);
   int *misc = reinterpret_cast<int *>(smem + plan.misc);
+  uint32_t *emx = reinterpret_cast<uint32_t *>(smem + plan.emx);   // DIRECT: [NW + 1] per warp, then per CTA
   uint16_t *fdir = reinterpret_cast<uint16_t *>(smem + plan.fdir);
   uint16_t *ring = reinterpret_cast<uint16_t *>(smem + plan.ring);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + plan.bars);
@@ -357,8 +378,15 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   // fields used inside the loops, held in registers (stores through the map pointers could
   // otherwise force reloads of the argument struct)
   const int pitch_e = p.pitch_e;
+  const int pitch_m = p.pitch_m ? p.pitch_m : p.pitch_e;
   const int64_t pstride = FWD ? p.pstride : 0;
   uint32_t *const Mrow = p.Mrow;
+  // DIRECT: the columns that exist in the caller's array, [0, Wa); rows are copied only there
+  const int Wa = (W + 7) & ~7;
+  const int cbeg = ext0 - KT;   // first staged column (a multiple of 8)
+  const int clo = DIRECT ? max(cbeg, 0) : cbeg;
+  const int chi = DIRECT ? min(cbeg + (int)(ROW_BYTES / 2), Wa) : cbeg + (int)(ROW_BYTES / 2);
+  const uint32_t COPY_BYTES = (uint32_t)(chi - clo) * 2;
 
   if (producer) {
     // ---- energy staging: rows of columns [ext0 - KT, ext0 - KT + BW), one bulk copy per lane ----
@@ -371,13 +399,13 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
       }
       const int rbeg = tt * KT;
       const int nrows = (H - rbeg < KT) ? H - rbeg : KT;
-      if (lane == 0) mbar_arrive_expect_tx(&full[slot], (uint32_t)(NP * nrows) * ROW_BYTES);
+      if (lane == 0) mbar_arrive_expect_tx(&full[slot], (uint32_t)(NP * nrows) * COPY_BYTES);
       __syncwarp();
       if (lane < nrows) {
 #pragma unroll
         for (int pl = 0; pl < NP; ++pl)
-          bulk_g2s(ring + (size_t)((slot * NP + pl) * KT + lane) * BW,
-                   Estage + pl * pstride + (size_t)(rbeg + lane) * pitch_e, ROW_BYTES, &full[slot]);
+          bulk_g2s(ring + (size_t)((slot * NP + pl) * KT + lane) * BW + (clo - cbeg),
+                   Estage + pl * pstride + (size_t)(rbeg + lane) * pitch_e + (clo - cbeg), COPY_BYTES, &full[slot]);
       }
     }
   } else if (!active) {
@@ -389,6 +417,9 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
     }
   } else {
     uint32_t k[V] = {0u, 0u, 0u, 0u};
+    uint32_t emax = 0u;   // DIRECT: running maximum of this lane's in-map energies (two uint16 halves)
+    const uint2 cm = make_uint2((oobm[0] ? 0u : 0xFFFFu) | (oobm[1] ? 0u : 0xFFFF0000u),
+                                (oobm[2] ? 0u : 0xFFFFu) | (oobm[3] ? 0u : 0xFFFF0000u));
     // The tile loop, compiled twice: EDGE warps hold columns outside the image and apply the
     // exclusion mask on every row; the others never test it.
     auto tiles = [&](auto edge_tag) {
@@ -424,11 +455,11 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
           // the row that needs them, off the dependent chain); bookkeeping only where a
           // super-tile or the image ends on its last row
           if (FWD) dp_rows_fwd<KT, BW, EDGE>(k, er, oobm);
-          else dp_rows<KT, BW, EDGE, LAT>(k, er, oobm);
+          else dp_rows<KT, BW, EDGE, LAT, DIRECT>(k, er, oobm, emax, cm);
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[slot]);   // this warp is done with the staged rows
           if (((r0 + KT) % KSS) == 0 || r0 + KT == H)
-            row_events<KSS>(r0 + KT - 1, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, gat0, gw, lastmin);
+            row_events<KSS>(r0 + KT - 1, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_m, ancT, OWC, gat0, gw, lastmin);
         } else {
           // first tile (row 0 has no predecessor) or a ragged last tile. Neither holds a row with
           // bookkeeping except the image's last row and the first tile's last row when KSS = KT:
@@ -441,13 +472,14 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
             k[1] = (hi8(ev.x) | (own_a + 1u)) | oobm[1];
             k[2] = (lo8(ev.y) | (own_a + 2u)) | oobm[2];
             k[3] = (hi8(ev.y) | (own_a + 3u)) | oobm[3];
+            emax_acc<DIRECT, EDGE>(emax, ev, cm);
           }
           if (FWD) dp_rows_n_fwd<KT, BW, EDGE>(k, er, oobm, t == 0 ? 1 : 0, n);
-          else dp_rows_n<KT, BW, EDGE, LAT>(k, er, oobm, t == 0 ? 1 : 0, n);
+          else dp_rows_n<KT, BW, EDGE, LAT, DIRECT>(k, er, oobm, t == 0 ? 1 : 0, n, emax, cm);
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[slot]);
           if (((r0 + n) % KSS) == 0 || r0 + n == H)
-            row_events<KSS>(r0 + n - 1, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_e, ancT, OWC, gat0, gw, lastmin);
+            row_events<KSS>(r0 + n - 1, k, H, W, c0, frame_base, cta_own, A, Mrow, pitch_m, ancT, OWC, gat0, gw, lastmin);
         }
         if (more) {
           const bool exch = CL && ((r0 + KT) % K2 == 0) && cs > 1;
@@ -486,7 +518,12 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
     };
     if (edge) tiles(std::integral_constant<bool, true>());
     else tiles(std::integral_constant<bool, false>());
+    if (DIRECT) {
+      const uint32_t m = __reduce_max_sync(0xffffffffu, max(emax & 0xFFFFu, emax >> 16));
+      if (lane == 0) emx[warp] = m;
+    }
   }
+  if (DIRECT && lane == 0 && (producer || !active)) emx[warp] = 0u;
   st.tiles += (uint32_t)nt;
   if (CL && nt > 0) st.exch += (uint32_t)((cs > 1) ? ((H - 1) / K2) : 0);
 
@@ -503,6 +540,11 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
     for (int w = 0; w <= NW; ++w) m = wmin[w] < m ? wmin[w] : m;
     if (CL) cg::this_cluster().map_shared_rank(cmin, 0)[rank] = m;   // pushed to rank 0
     else cmin[0] = m;
+    if (DIRECT) {
+      uint32_t e = 0u;
+      for (int w = 0; w <= NW; ++w) e = max(e, emx[w]);
+      cg::this_cluster().map_shared_rank(emx, 0)[NW + 1 + rank] = e;
+    }
   }
   group_sync<CL>();
 
@@ -511,6 +553,16 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
     int ok = !p.gated;
     unsigned long long best = ~0ull;
     for (int r = 0; r < cs; ++r) best = cmin[r] < best ? cmin[r] : best;
+    if (DIRECT && ok) {
+      // the 24-bit keys hold the seam sums only while H * max(e) < 2^24; otherwise this result is
+      // void and the wide-cost search, launched next, takes the map
+      uint32_t e = 0u;
+      for (int r = 0; r < cs; ++r) e = max(e, emx[NW + 1 + r]);
+      if ((uint64_t)e * (uint64_t)H >= ((uint64_t)1 << 24)) {
+        ok = 0;
+        if (p.gate) atomicOr(p.gate, ERR_ENERGY_RANGE);
+      }
+    }
     int j = (int)(best & 0xFFFFFFFFull);
     if (ok && (j < 0 || j >= W)) { ok = 0; atomicOr(p.err, ERR_BAD_SEAM); }
     if (ok && gw) {
@@ -566,9 +618,16 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
     if (s >= S) return;
     int x0 = jb0[s] - FILLW / 2;
     x0 -= ((x0 % 8) + 8) % 8;
+    int x1 = x0 + FILLW + 8;
+    if (DIRECT) {   // only the caller's columns
+      x0 = max(x0, 0);
+      x1 = min(x1, Wa);
+      if (x1 <= x0) return;
+    }
     for (int i = s * KSS + lane; i < s * KSS + KSS && i < H; i += 32)
 #pragma unroll
-      for (int pl = 0; pl < NP; ++pl) bulk_prefetch_l2(Ef + pl * pstride + (size_t)i * pitch_e + x0, FILLW * 2 + 16);
+      for (int pl = 0; pl < NP; ++pl)
+        bulk_prefetch_l2(Ef + pl * pstride + (size_t)i * pitch_e + x0, (uint32_t)(x1 - x0) * 2);
   };
   auto unpack = [](const EVec &v, uint32_t (&x)[FV]) {
     const uint32_t *w = reinterpret_cast<const uint32_t *>(&v);
@@ -591,12 +650,16 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
     uint32_t m[FV], oob[FV];
 #pragma unroll
     for (int u = 0; u < FV; ++u) oob[u] = (xc + u < 0 || xc + u >= W) ? SENT : 0u;
+    // DIRECT: a lane's FV columns lie wholly inside or wholly outside the caller's [0, Wa)
+    const bool xin = !DIRECT || (xc >= 0 && xc + FV <= Wa);
     if (s == 0) {
-      unpack(*reinterpret_cast<const EVec *>(Ef + xc), m);
+      EVec v0{};
+      if (xin) v0 = *reinterpret_cast<const EVec *>(Ef + xc);
+      unpack(v0, m);
     } else {
 #pragma unroll
       for (int q = 0; q < FV / 4; ++q) {
-        const uint4 a = *reinterpret_cast<const uint4 *>(Mrow + (size_t)s * pitch_e + xc + 4 * q);
+        const uint4 a = *reinterpret_cast<const uint4 *>(Mrow + (size_t)s * pitch_m + xc + 4 * q);
         m[4 * q] = a.x; m[4 * q + 1] = a.y; m[4 * q + 2] = a.z; m[4 * q + 3] = a.w;
       }
     }
@@ -615,7 +678,10 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
         const int i = rbeg + r;
 #pragma unroll
         for (int pl = 0; pl < NP; ++pl)
-          if (i < re) eb[pl][r] = *reinterpret_cast<const EVec *>(Ef + pl * pstride + (size_t)i * pitch_e + xc);
+          if (i < re) {
+            if (xin) eb[pl][r] = *reinterpret_cast<const EVec *>(Ef + pl * pstride + (size_t)i * pitch_e + xc);
+            else eb[pl][r] = EVec{};
+          }
       }
     };
     auto run_chunk = [&](const EVec (&eb)[NP][CH], int rbeg) {

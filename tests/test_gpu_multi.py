@@ -86,12 +86,39 @@ def test_multi_uhd(dev, shape):
     _check(dev, maps)
 
 
+@pytest.mark.parametrize("W", [904, 900])
+def test_multi_range_boundary(dev, W):
+    """The 24-bit range check at its exact boundary, H * max(e) = 2^24 - 1 (fast search) against
+    2^24 (wide-cost search), for maps read in place (W a multiple of 8) and maps that are copied
+    first (W = 900, and a map whose base is not 16-byte aligned); every seam and cost equals the
+    oracle's."""
+    H = 1024
+    rng = np.random.default_rng(W)
+    lim = ((1 << 24) - 1) // H          # 16383: the largest energy the 24-bit search takes at H = 1024
+    maps = []
+    for top in (lim, lim + 1):
+        m = rng.integers(0, top, size=(H, W)).astype(np.uint16)
+        m[rng.integers(0, H), rng.integers(0, W)] = top   # one cell at the boundary value
+        maps.append(m)
+    maps.append(np.full((H, W), lim + 1, dtype=np.uint16))
+    _check(dev, maps)
+    # a map whose rows start 2 bytes past a 16-byte boundary (a view into a larger buffer)
+    buf = torch.from_numpy(np.concatenate([np.zeros(1, np.uint16), maps[1].ravel()])).to(dev)
+    view = buf[1:].view(H, W)
+    got_s, got_c = sc.find_seam_multi([view, torch.from_numpy(maps[0]).to(dev)])
+    sc.check()
+    for k, m in enumerate([maps[1], maps[0]]):
+        s_ref, c_ref = oracle.dp_seam(m)
+        assert int(got_c[k]) == c_ref
+        np.testing.assert_array_equal(got_s[k].cpu().numpy(), s_ref)
+
+
 def test_multi_mixed_energy_ranges(dev):
     """Maps of one batch on both sides of the 24-bit cost limit: each map's range is checked on its
     own, the over-range ones go to the wide-cost search, and every seam and cost equals the
     oracle's."""
     rng = np.random.default_rng(90)
-    H, W = 1200, 900
+    H, W = 1200, 904
     maps = [rng.integers(0, 1531, size=(H, W)), np.full((H, W), 65535), rng.integers(0, 65536, size=(H, W)),
             rng.integers(0, 3, size=(H, W)), rng.integers(65530, 65536, size=(H, W)), np.full((H, W), 9)]
     _check(dev, [m.astype(np.uint16) for m in maps])
