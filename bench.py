@@ -180,27 +180,11 @@ def cpu_info():
     return {"host_cores": os.cpu_count(), "cpu_model": model or platform.machine()}
 
 
-def l2_peak(torch, dev):
-    """Copy bandwidth with both buffers inside L2 (2 x 16 MiB against a 126 MB L2), repeated 50
-    times per CUDA-event bracket, best of 5: the denominator of the L2 roofline fractions (read +
-    write bytes per second)."""
-    n = 4 << 20   # float32 elements: 16 MiB
-    a = torch.ones(n, dtype=torch.float32, device=dev)
-    b = torch.empty_like(a)
-    for _ in range(10):
-        b.copy_(a)
-    torch.cuda.synchronize(dev)
-    best = 0.0
-    for _ in range(5):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(50):
-            b.copy_(a)
-        e1.record()
-        torch.cuda.synchronize(dev)
-        best = max(best, 2 * 4 * n * 50 / (e0.elapsed_time(e1) / 1e3) / 1e9)
-    return best
+def l2_peak(sc):
+    """The L2 copy bandwidth, the denominator of the L2 roofline fractions: two 32 MiB buffers
+    (inside the 126 MB L2) copied 40 times within one launch of the library's probe, read + write
+    bytes over the CUDA-event time of that launch; best of 3."""
+    return max(sc.probe_copy_bandwidth(32 << 20, 40) for _ in range(3))
 
 
 def _workload():
@@ -815,7 +799,7 @@ def run_native(a):
     dp_bytes_per_launch = dp_bytes / max(seams, 1)
     achieved = (dp_bytes * a.steps) / (dp_ms / 1000.0) / 1e9 if dp_ms > 0 else None
     peak, peak_src = _peaks()
-    l2 = l2_peak(torch, dev)
+    l2 = l2_peak(sc)
     traffic = _traffic_from_profile()
 
     line = {

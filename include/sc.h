@@ -82,6 +82,16 @@ int sc_timing_enable(int on);
 int sc_timing_reset(void);
 int sc_timing_read(const char *kernel, double *total_ms, int64_t *launches);
 
+/* Copy-bandwidth probe (instrumentation, no counterpart in the paper): allocates two device
+ * buffers of `bytes` each, copies one into the other `reps` times within ONE kernel launch (so the
+ * time is the copies' own, not the gaps between short launches), times that launch with CUDA events
+ * on the legacy default stream after a warm-up launch, and returns read + write bytes per second
+ * in GB/s. With both buffers inside L2 (2 x 32 MiB against a 126 MB L2) it measures the L2 copy
+ * bandwidth; with buffers far larger than L2, the HBM copy bandwidth. Synchronous; frees what it
+ * allocates. Errors: SC_EINVAL for bytes < 4096 or not a multiple of 16, reps outside 1..10000;
+ * SC_ECUDA for a failed CUDA call. */
+int sc_probe_copy_bandwidth(size_t bytes, int reps, double *gbs_out);
+
 /* ---- e1 energy (section "Energy Mapping", item e1) ----
  * img:        device, H x W x C uint8, row-major.
  * energy_out: device, H x W uint16, row-major; written completely.

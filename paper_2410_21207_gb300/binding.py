@@ -83,6 +83,7 @@ def load(path: Optional[str] = None):
                 "sc_timing_enable": ([I], I),
                 "sc_timing_reset": ([], I),
                 "sc_timing_read": ([ctypes.c_char_p, P, P], I),
+                "sc_probe_copy_bandwidth": ([ctypes.c_size_t, I, P], I),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -393,6 +394,14 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+def probe_copy_bandwidth(nbytes: int, reps: int) -> float:
+    """sc_probe_copy_bandwidth: GB/s (read + write) of `reps` copies of an nbytes buffer in one launch."""
+    _torch()
+    g = ctypes.c_double(0.0)
+    _raise(load().sc_probe_copy_bandwidth(ctypes.c_size_t(nbytes), int(reps), ctypes.byref(g)))
+    return g.value
 
 
 def timing_enable(on: bool = True) -> None:

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -482,10 +483,19 @@ int sc_find_seam_multi(const uint16_t *const *energies, int n, int H, int W, int
     a.err = ws.flags.p;
     a.gate = ws.gates.p + k;
   }
-  SC_CUDA(cudaMemcpyAsync(ws.dargs.p, h.data(), n * sizeof(DpArgs), cudaMemcpyHostToDevice, st));
-  SC_CUDA(timed("dp_multi", st, [&] { return launch_dp_multi(ws.dargs.p, n, H, W, st); }));
+  // up to MULTI_INLINE maps' arguments travel in the launches themselves; more go through a copy
+  std::unique_ptr<MultiArgs> inl;
+  if (n <= MULTI_INLINE) {
+    inl.reset(new MultiArgs());
+    for (int k = 0; k < n; ++k) inl->a[k] = h[k];
+  } else {
+    SC_CUDA(cudaMemcpyAsync(ws.dargs.p, h.data(), n * sizeof(DpArgs), cudaMemcpyHostToDevice, st));
+  }
+  SC_CUDA(timed("dp_multi", st, [&] { return launch_dp_multi(ws.dargs.p, inl.get(), n, H, W, st); }));
   // maps whose seam sums may not fit 24 bits (gates set by the search or the copy) were left over
-  SC_CUDA(timed("dp_wide", st, [&] { return launch_dp_wide_multi(ws.dargs.p, n, H, W, ws.wdirs.p, ws.wanc.p, st); }));
+  SC_CUDA(timed("dp_wide", st, [&] {
+    return launch_dp_wide_multi(ws.dargs.p, inl.get(), n, H, W, ws.wdirs.p, ws.wanc.p, st);
+  }));
   return SC_OK;
 }
 

@@ -20,10 +20,11 @@ namespace sc {
 constexpr int MULTI_FILL_WARPS = 7;
 
 template <int NW, int KT>
-__global__ void __launch_bounds__(Geo<NW, KT, true>::THREADS, NW == 8 ? 2 : 4) k_dp_multi(const DpArgs *__restrict__ ps) {
+__global__ void __launch_bounds__(Geo<NW, KT, true>::THREADS, NW == 8 ? 2 : 4) k_dp_multi(const DpArgs *__restrict__ ps,
+                                                                                          const __grid_constant__ MultiArgs inl) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int img = blockIdx.x / cg::this_cluster().num_blocks();
-  const DpArgs p = ps[img];
+  const DpArgs p = ps ? ps[img] : inl.a[img];
   const int S = (p.H + KS - 1) / KS;
   search_init<NW, KT, true, MULTI_FILL_WARPS, false, KS, true>(smem, S);
   cg::this_cluster().sync();
@@ -49,7 +50,7 @@ namespace {
 struct MultiShape {
   int nw, kt, ow;
   cudaError_t (*configure)();
-  cudaError_t (*launch)(const DpArgs *, int, int, int, cudaStream_t);
+  cudaError_t (*launch)(const DpArgs *, const MultiArgs *, int, int, int, cudaStream_t);
   cudaError_t (*capacity)(int, int, int *);
   size_t (*smem)(int);
 };
@@ -87,14 +88,15 @@ void multi_cfg(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at, int n, int H, i
 }
 
 template <int NW, int KT>
-cudaError_t multi_launch(const DpArgs *dargs, int n, int H, int cs, cudaStream_t st) {
+cudaError_t multi_launch(const DpArgs *dargs, const MultiArgs *inl, int n, int H, int cs, cudaStream_t st) {
   cudaError_t e = multi_configure<NW, KT>();
   if (e != cudaSuccess) return e;
   if (multi_smem<NW, KT>(H) > 232448) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute at[1];
   multi_cfg<NW, KT>(cfg, at, n, H, cs, st);
-  return cudaLaunchKernelEx(&cfg, k_dp_multi<NW, KT>, dargs);
+  static const MultiArgs none{};
+  return cudaLaunchKernelEx(&cfg, k_dp_multi<NW, KT>, inl ? nullptr : dargs, inl ? *inl : none);
 }
 
 template <int NW, int KT>
@@ -178,11 +180,11 @@ cudaError_t dp_multi_capacity(int H, int W, int *n_out) {
   return kShapes[k].capacity(H, cs, n_out);
 }
 
-cudaError_t launch_dp_multi(const DpArgs *dargs_dev, int n, int H, int W, cudaStream_t st) {
+cudaError_t launch_dp_multi(const DpArgs *dargs_dev, const MultiArgs *inl, int n, int H, int W, cudaStream_t st) {
   const int k = pick_shape(H, W);
-  if (k < 0 || n < 1) return cudaErrorInvalidValue;
+  if (k < 0 || n < 1 || (inl && n > MULTI_INLINE) || (!inl && !dargs_dev)) return cudaErrorInvalidValue;
   const int cs = clusters_for(kShapes[k], W);
-  return kShapes[k].launch(dargs_dev, n, H, cs, st);
+  return kShapes[k].launch(dargs_dev, inl, n, H, cs, st);
 }
 
 }  // namespace sc

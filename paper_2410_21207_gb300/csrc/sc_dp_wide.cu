@@ -260,11 +260,12 @@ __global__ void __launch_bounds__(WIDE_THREADS, 1) k_dp_wide(DpArgs p, uint32_t 
 
 // map blockIdx.x of n, each with its own scratch slices
 template <bool FWD>
-__global__ void __launch_bounds__(WIDE_THREADS, 1) k_dp_wide_multi(const DpArgs *__restrict__ ps, uint32_t *dirs,
-                                                                   uint16_t *anc, size_t dirs_stride,
+__global__ void __launch_bounds__(WIDE_THREADS, 1) k_dp_wide_multi(const DpArgs *__restrict__ ps,
+                                                                   const __grid_constant__ MultiArgs inl,
+                                                                   uint32_t *dirs, uint16_t *anc, size_t dirs_stride,
                                                                    size_t anc_stride) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const DpArgs p = ps[blockIdx.x];
+  const DpArgs p = ps ? ps[blockIdx.x] : inl.a[blockIdx.x];
   wide_search<FWD>(p, dirs + blockIdx.x * dirs_stride, anc + blockIdx.x * anc_stride, smem);
 }
 
@@ -290,14 +291,16 @@ cudaError_t launch_dp_wide(const DpArgs &a, uint32_t *dirs, uint16_t *anc, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_dp_wide_multi(const DpArgs *dargs_dev, int n, int H, int W, uint32_t *dirs, uint16_t *anc,
-                                 cudaStream_t st) {
-  if (n < 1 || W > 4 * 2 * WIDE_THREADS) return cudaErrorInvalidValue;
+cudaError_t launch_dp_wide_multi(const DpArgs *dargs_dev, const MultiArgs *inl, int n, int H, int W, uint32_t *dirs,
+                                 uint16_t *anc, cudaStream_t st) {
+  if (n < 1 || W > 4 * 2 * WIDE_THREADS || (inl && n > MULTI_INLINE) || (!inl && !dargs_dev))
+    return cudaErrorInvalidValue;
   const size_t smem = wide_smem_bytes(H, W);
   cudaError_t e = wide_configure(k_dp_wide_multi<false>, smem);
   if (e != cudaSuccess) return e;
-  k_dp_wide_multi<false><<<n, WIDE_THREADS, smem, st>>>(dargs_dev, dirs, anc, wide_dirs_words(H, W),
-                                                        wide_anc_elems(H, W));
+  static const MultiArgs none{};
+  k_dp_wide_multi<false><<<n, WIDE_THREADS, smem, st>>>(inl ? nullptr : dargs_dev, inl ? *inl : none, dirs, anc,
+                                                        wide_dirs_words(H, W), wide_anc_elems(H, W));
   return cudaGetLastError();
 }
 

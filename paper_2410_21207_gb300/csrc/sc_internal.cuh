@@ -88,8 +88,9 @@ cudaError_t launch_dp(const DpArgs &a, cudaStream_t st);   // forward energy whe
 // direction words and wide_anc_elems(H, W) uint16 ancestors. Forward energy when a.pstride > 0
 // (W <= 4096); the multi-map form takes a device array of n DpArgs of one size (e1 only).
 cudaError_t launch_dp_wide(const DpArgs &a, uint32_t *dirs, uint16_t *anc, cudaStream_t st);
-cudaError_t launch_dp_wide_multi(const DpArgs *dargs_dev, int n, int H, int W, uint32_t *dirs, uint16_t *anc,
-                                 cudaStream_t st);
+struct MultiArgs;
+cudaError_t launch_dp_wide_multi(const DpArgs *dargs_dev, const MultiArgs *inl, int n, int H, int W, uint32_t *dirs,
+                                 uint16_t *anc, cudaStream_t st);
 size_t wide_dirs_words(int H, int W);
 size_t wide_anc_elems(int H, int W);
 int dp_forward_max_width();                                 // widest map the forward search takes
@@ -97,7 +98,13 @@ int dp_forward_max_width();                                 // widest map the fo
 // are read in place (E = row 0, column 0; pitch_e a multiple of 8; 16-byte aligned rows) and each
 // map's 24-bit cost range is checked in the kernel: a map that fails sets its gate and is left to
 // launch_dp_wide_multi
-cudaError_t launch_dp_multi(const DpArgs *dargs_dev, int n, int H, int W, cudaStream_t st);
+// Up to MULTI_INLINE maps' arguments travel in the launch itself (a __grid_constant__ parameter):
+// no host-to-device copy per call. `inl` (host) is used when non-null, else `dargs_dev`.
+constexpr int MULTI_INLINE = 64;
+struct MultiArgs {
+  DpArgs a[MULTI_INLINE];
+};
+cudaError_t launch_dp_multi(const DpArgs *dargs_dev, const MultiArgs *inl, int n, int H, int W, cudaStream_t st);
 // how many H x W searches of launch_dp_multi are resident on the GPU at once
 cudaError_t dp_multi_capacity(int H, int W, int *n_out);
 // tile shape of launch_dp_multi: (compute warps per CTA, tile rows), (0, 0) = automatic;

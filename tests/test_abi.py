@@ -62,6 +62,9 @@ def test_argument_errors_are_synchronous():
     assert lib.sc_find_seam_static(fake, 4000, 4000, fake, P(0), P(0)) == binding.SC_EINVAL
     assert b"bytes of scratch" in lib.sc_last_error()
     assert lib.sc_find_seam_static_selftest(0, 10, fake, P(0), P(0)) == binding.SC_EINVAL
+    g = ctypes.c_double(0.0)
+    assert lib.sc_probe_copy_bandwidth(ctypes.c_size_t(100), 1, ctypes.byref(g)) == binding.SC_EINVAL
+    assert lib.sc_probe_copy_bandwidth(ctypes.c_size_t(1 << 20), 0, ctypes.byref(g)) == binding.SC_EINVAL
     assert lib.sc_find_seam_static_selftest(1000, 0, fake, P(0), P(0)) == binding.SC_EINVAL
     assert lib.sc_find_seam_multi_shape(5, 8) == binding.SC_EINVAL
     assert lib.sc_find_seam_multi_shape(0, 0) == binding.SC_OK
