@@ -242,15 +242,20 @@ def find_seam_multi(energies):
     es = list(energies)
     if not es:
         raise ValueError("need at least one energy map")
-    H, W = es[0].shape
-    for e in es:
-        if (e.device.type != "cuda" or e.dtype != torch.uint16 or e.dim() != 2 or not e.is_contiguous()
-                or tuple(e.shape) != (H, W) or e.device != es[0].device):
+    e0 = es[0]
+    if e0.device.type != "cuda" or e0.dim() != 2:
+        raise ValueError("energies must be contiguous H x W uint16 CUDA tensors of one shape and device")
+    H, W = e0.shape
+    shape0, dev0, u16 = e0.shape, e0.get_device(), torch.uint16
+    ptrs = []
+    for e in es:   # one pass, cheap checks: this runs on every call
+        if e.dtype is not u16 or e.shape != shape0 or not e.is_contiguous() or e.get_device() != dev0:
             raise ValueError("energies must be contiguous H x W uint16 CUDA tensors of one shape and device")
+        ptrs.append(e.data_ptr())
     n = len(es)
-    seams = torch.empty((n, H), dtype=torch.int32, device=es[0].device)
-    costs = torch.empty(n, dtype=torch.int64, device=es[0].device)
-    ptrs = (ctypes.c_void_p * n)(*[e.data_ptr() for e in es])
+    seams = torch.empty((n, H), dtype=torch.int32, device=e0.device)
+    costs = torch.empty(n, dtype=torch.int64, device=e0.device)
+    ptrs = (ctypes.c_void_p * n)(*ptrs)
     _raise(load().sc_find_seam_multi(ptrs, n, H, W, _ptr(seams), _ptr(costs), _stream(torch, es[0].device)))
     return seams, costs
 
