@@ -368,15 +368,17 @@ class BatchPlan:
     (optionally autotuned) and replayed by run(). The input tensors must stay alive and keep their
     storage; their contents may change between runs."""
 
-    def __init__(self, imgs: Sequence, targets: Sequence[Tuple[int, int]], autotune: bool = False,
+    def __init__(self, imgs: Sequence, targets: Sequence[Tuple[int, int]], autotune=False,
                  with_log: bool = False):
+        """autotune: False/0 default configuration, True/1 time the configurations and balancing
+        variants, 2 default configuration with the heaviest images on 4-CTA clusters."""
         torch = _torch()
         self.imgs = list(imgs)
         self.descs, self.outs, self.logs = _batch_descs(self.imgs, targets, with_log)
         self.device = self.imgs[0].device
         h = ctypes.c_void_p(0)
         _raise(load().sc_batch_plan_create(ctypes.cast(self.descs, ctypes.c_void_p), len(self.imgs),
-                                           1 if autotune else 0, _stream(torch, self.device), ctypes.byref(h)))
+                                           int(autotune), _stream(torch, self.device), ctypes.byref(h)))
         self._h = h
 
     def run(self):

@@ -659,6 +659,10 @@ namespace sc {
 
 // ---- batched carve (one persistent launch; images wider than a CTA go to the cluster path) ----
 static const BatchCfg kBatchCfgs[] = {{15, 16}, {15, 8}, {12, 8}, {12, 16}, {8, 16}, {8, 8}, {8, 32}};
+// load-balancing variants the autotuner times on top of its fastest configuration: images whose
+// work exceeds thr x the mean share per SM go to clusters of 4 (higher tier) or 2 CTAs
+static const BatchCfg kBalanceCfgs[] = {{0, 0, 0, 0.f, 2, 1.0f}, {0, 0, 0, 0.f, 2, 1.6f}, {0, 0, 4, 1.6f, 0, 0.f},
+                                        {0, 0, 4, 2.0f, 2, 1.0f}};
 
 int batch_need_width(const sc_image_desc &d) {
   const int nh = d.H - d.target_h;
@@ -701,6 +705,19 @@ int batch_cluster_size(const sc_image_desc &d) {
   return (batch_need_width(d) + own - 1) / own;
 }
 
+// pixels of every searched map summed over an image's seams (the carving work)
+static double item_work(const sc_image_desc &d) {
+  const double nv = d.W - d.target_w, nh = d.H - d.target_h;
+  return nv * d.H * (d.W - (nv - 1) / 2.0) + nh * d.target_w * (d.H - (nh - 1) / 2.0);
+}
+
+static int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return sms;
+}
+
 // Lays out every batched image's scratch in one pool (offsets; `pool` may be null to size it):
 // images that one CTA of configuration c covers first, then the wider ones by cluster size.
 void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned char *pool, BatchSetup &b) {
@@ -711,13 +728,28 @@ void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned
   size_t off = 0;
   const int limit = batch_width_limit(c.nw, c.kt);
   std::vector<int> wide;
+  // the images that would hold up the batch on one CTA each: carving work above thr x the mean
+  // share per SM goes to a cluster (the batch then ends when the average SM does, not when the
+  // largest image does)
+  std::vector<int> cs_bal(n, 1);
+  if (c.cs_hi > 1 || c.cs_lo > 1) {
+    const int sms = device_sms();
+    double total = 0.0;
+    for (int k = 0; k < n; ++k) total += item_work(descs[k]);
+    const double share = sms > 0 ? total / sms : 0.0;
+    for (int k = 0; k < n && share > 0.0; ++k) {
+      const double w = item_work(descs[k]);
+      if (c.cs_hi > 1 && w > share * c.thr_hi) cs_bal[k] = c.cs_hi;
+      else if (c.cs_lo > 1 && w > share * c.thr_lo) cs_bal[k] = c.cs_lo;
+    }
+  }
   for (int k = 0; k < n; ++k) {
     const sc_image_desc &d = descs[k];
     const int nh0 = d.H - d.target_h;
     const int rows0 = (nh0 > 0 && d.target_w > d.H) ? d.target_w : d.H;
     // the refreshed pairs of a pass live in the CTA's staging ring between searches
     const size_t ring_bytes = (size_t)3 * c.kt * (c.nw * (128 - 2 * c.kt) + 2 * c.kt) * 2;
-    if (batch_need_width(d) > limit || (size_t)rows0 * 4 > ring_bytes) {
+    if (batch_need_width(d) > limit || (size_t)rows0 * 4 > ring_bytes || cs_bal[k] > 1) {
       wide.push_back(k);
       continue;
     }
@@ -727,7 +759,7 @@ void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned
   }
   for (int k : wide) {
     const sc_image_desc &d = descs[k];
-    const int cs = batch_cluster_size(d);
+    const int cs = std::max(batch_cluster_size(d), cs_bal[k]);
     if (cs > MAX_CLUSTER) {
       b.fallback.push_back(k);
       continue;
@@ -800,6 +832,17 @@ struct BatchRun {
   BatchCfg cfg{15, 16};
   int grid = 1;
   std::vector<int> cl_clusters;   // clusters launched per group
+  // the cluster launches run beside the one-CTA launch on a second stream (fork and join events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  BatchRun() = default;
+  BatchRun(const BatchRun &) = delete;
+  BatchRun &operator=(const BatchRun &) = delete;
+  ~BatchRun() {
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (side) cudaStreamDestroy(side);
+  }
 };
 
 // Allocates and uploads everything one batched launch needs (synchronous upload).
@@ -820,15 +863,23 @@ static int batch_prepare(BatchRun &r, const sc_image_desc *descs, int n, const B
   SC_CUDA(cudaGetDevice(&dev));
   SC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int per_sm = batch_blocks_per_sm(c.nw, c.kt, r.setup.Smax);
-  r.grid = sms * per_sm;
-  if (r.grid > nb) r.grid = nb;
-  if (r.grid < 1) r.grid = 1;
   r.cl_clusters.assign(ng, 1);
+  int cl_sms = 0;
   for (int g = 0; g < ng; ++g) {
     int cap = 0;
     SC_CUDA(batch_cl_capacity(r.setup.cl[g].cs, r.setup.cl[g].Smax, &cap));
     const int ni = (int)r.setup.cl[g].items.size();
     r.cl_clusters[g] = cap < 1 ? 1 : (cap < ni ? cap : ni);
+    cl_sms += r.cl_clusters[g] * r.setup.cl[g].cs;
+  }
+  // the one-CTA launch leaves the clusters' SMs to them: the two run side by side
+  r.grid = (sms - (nb > 0 ? std::min(cl_sms, sms - 1) : 0)) * per_sm;
+  if (r.grid > nb) r.grid = nb;
+  if (r.grid < 1) r.grid = 1;
+  if (ng > 0 && nb > 0 && !r.side) {
+    SC_CUDA(cudaStreamCreateWithFlags(&r.side, cudaStreamNonBlocking));
+    SC_CUDA(cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming));
+    SC_CUDA(cudaEventCreateWithFlags(&r.join, cudaEventDisableTiming));
   }
   return SC_OK;
 }
@@ -839,17 +890,28 @@ static cudaError_t batch_launches(BatchRun &r, cudaStream_t st, int *err) {
   const int ng = (int)r.setup.cl.size();
   cudaError_t e = cudaMemsetAsync(r.queue.p, 0, (size_t)(1 + ng) * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  if (nb) {
-    e = launch_batch(r.cfg.nw, r.cfg.kt, r.items.p, nb, r.setup.Smax, r.grid, r.queue.p, err, st);
-    if (e != cudaSuccess) return e;
+  // with both kinds, the cluster launches go on the side stream and run beside the one-CTA launch
+  const bool fork = ng > 0 && nb > 0 && r.side;
+  cudaStream_t cst = fork ? r.side : st;
+  if (fork) {
+    if ((e = cudaEventRecord(r.fork, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(r.side, r.fork, 0)) != cudaSuccess) return e;
   }
   size_t base = nb;
   for (int g = 0; g < ng; ++g) {
     const ClusterGroup &G = r.setup.cl[g];
     e = launch_batch_cl(r.items.p + base, (int)G.items.size(), G.cs, G.Smax, r.cl_clusters[g], r.queue.p + 1 + g,
-                        err, st);
+                        err, cst);
     if (e != cudaSuccess) return e;
     base += G.items.size();
+  }
+  if (nb) {
+    e = launch_batch(r.cfg.nw, r.cfg.kt, r.items.p, nb, r.setup.Smax, r.grid, r.queue.p, err, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (fork) {
+    if ((e = cudaEventRecord(r.join, r.side)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(st, r.join, 0)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -910,29 +972,51 @@ int sc_batch_plan_create(const sc_image_desc *descs, int n, int autotune, void *
   p->descs.assign(descs, descs + n);
   p->err = device_error_word();
   if (!p->err) { delete p; return fail(SC_ECUDA, "cannot allocate the device error word"); }
+  if (autotune < 0 || autotune > 2) { delete p; return fail(SC_EINVAL, "autotune must be 0, 1 or 2"); }
   BatchCfg best = default_batch_cfg(descs, n);
-  if (autotune) {
-    // time every configuration that batches as many images as the default, on the real batch
+  if (autotune == 2) {   // the default configuration with the heaviest images on 4-CTA clusters
+    best.cs_hi = 4;
+    best.thr_hi = 1.6f;
+  }
+  if (autotune == 1) {
+    // time every configuration that batches as many images as the default, on the real batch;
+    // then, for the fastest, the load-balancing variants (the heaviest images on clusters)
     BatchSetup b0;
     batch_layout(descs, n, best, nullptr, b0);
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
     SC_CUDA(cudaEventCreate(&e0));
     SC_CUDA(cudaEventCreate(&e1));
+    auto trial_ms = [&](const BatchCfg &c, float *ms) -> int {
+      BatchRun trial;
+      int rc2 = batch_prepare(trial, descs, n, c);
+      if (!rc2) rc2 = batch_enqueue(trial, descs, st, p->err);
+      if (rc2) return rc2;
+      SC_CUDA(cudaEventRecord(e0, st));
+      if ((rc2 = batch_enqueue(trial, descs, st, p->err))) return rc2;
+      SC_CUDA(cudaEventRecord(e1, st));
+      SC_CUDA(cudaEventSynchronize(e1));
+      SC_CUDA(cudaEventElapsedTime(ms, e0, e1));
+      return SC_OK;
+    };
     for (const BatchCfg &c : kBatchCfgs) {
       BatchSetup b;
       batch_layout(descs, n, c, nullptr, b);
       if (b.items.size() < b0.items.size()) continue;
       if (batch_smem_bytes(c.nw, c.kt, b.Smax) > 232448 - 1024) continue;
-      BatchRun trial;
-      if ((rc = batch_prepare(trial, descs, n, c))) { delete p; return rc; }
-      if ((rc = batch_enqueue(trial, descs, st, p->err))) { delete p; return rc; }
-      SC_CUDA(cudaEventRecord(e0, st));
-      if ((rc = batch_enqueue(trial, descs, st, p->err))) { delete p; return rc; }
-      SC_CUDA(cudaEventRecord(e1, st));
-      SC_CUDA(cudaEventSynchronize(e1));
       float ms = 0.f;
-      SC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if ((rc = trial_ms(c, &ms))) { delete p; return rc; }
+      if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    const BatchCfg base = best;
+    for (const BatchCfg &v : kBalanceCfgs) {
+      BatchCfg c = base;
+      c.cs_hi = v.cs_hi; c.thr_hi = v.thr_hi; c.cs_lo = v.cs_lo; c.thr_lo = v.thr_lo;
+      BatchSetup b;
+      batch_layout(descs, n, c, nullptr, b);
+      if (!b.fallback.empty() || b.cluster_images() == b0.cluster_images()) continue;   // nothing moves
+      float ms = 0.f;
+      if ((rc = trial_ms(c, &ms))) { delete p; return rc; }
       if (ms < best_ms) { best_ms = ms; best = c; }
     }
     cudaEventDestroy(e0);

@@ -23,6 +23,12 @@ int static_pending_errors(int *bits);
 
 struct BatchCfg {
   int nw, kt;
+  // load balance: an image whose carving work exceeds thr x the whole batch's mean share per SM is
+  // carved by a cluster of cs CTAs instead of one CTA (cs 0: off); the higher tier is tested first
+  int cs_hi = 0;
+  float thr_hi = 0.f;
+  int cs_lo = 0;
+  float thr_lo = 0.f;
 };
 // images wider than one CTA, carved by the cluster-per-image batched kernel (one group per
 // cluster size)

@@ -121,3 +121,22 @@ def test_batch_plan_with_wide_images_replays(dev):
         sc.check()
         _check(imgs, targets, plan.outs, plan.logs)
     plan.close()
+
+
+def test_balanced_plan_runs_clusters_beside_one_cta_kernel(dev):
+    """A batch dominated by one large image: with load balancing (autotune = 2) the large image is
+    carved by a 4-CTA cluster launched beside the one-CTA kernel that carves the small ones (two
+    graph branches); every image still equals the oracle's carve of it alone, on two replays."""
+    big = synth.gen_image(1000, 700, 8, 20, 200, 2024)
+    smalls = [synth.gen_image(120 + 9 * k, 90 + 5 * k, 3, 10, 40, 300 + k) for k in range(24)]
+    imgs = [big] + smalls
+    targets = [(700, 700)] + [(im.shape[1] - 8 - k % 5, im.shape[0]) for k, im in enumerate(smalls)]
+    d = [torch.from_numpy(i).to(dev) for i in imgs]
+    plan = sc.BatchPlan(d, targets, autotune=2, with_log=True)
+    info = plan.info()
+    assert info["cluster_path"] == 1 and info["batched"] == len(smalls)
+    for _ in range(2):
+        plan.run()
+        sc.check()
+        _check(imgs, targets, plan.outs, plan.logs)
+    plan.close()
