@@ -171,6 +171,35 @@ def test_carve_generated_multi_cta(dev):
     _carve_cmp(dev, img, 650, 300)
 
 
+@pytest.mark.parametrize("H", [4111, 4112])
+def test_carve_tall_heavy_edges(dev, H):
+    """Tall carves (4111 and 4112 rows, 64-row super-tiles' ragged ends, seam sums past 2^23)
+    with maximum-energy pixels next to both image edges and random ones in between: both equal the
+    oracle (seam log, costs, bytes)."""
+    yy, xx = np.mgrid[0:H, 0:70]
+    img = (((yy + xx) & 1) * 255).astype(np.uint8)[:, :, None].repeat(4, axis=2)   # e1 = 2040 everywhere
+    img[:, 30:40] = np.random.default_rng(H).integers(0, 256, size=(H, 10, 4)).astype(np.uint8)
+    _carve_cmp(dev, img, 66, H)
+
+
+@pytest.mark.parametrize("top", [8191, 8192])
+def test_find_seam_heavy_edges(dev, top):
+    """Caller maps with their largest energy (seam sums on either side of 2^23 at H = 1024) in the
+    edge columns and ties everywhere else: seam and cost equal the oracle's, for map widths that end
+    inside a lane and on a lane boundary."""
+    rng = np.random.default_rng(top)
+    for W in (257, 256, 1029, 1920):
+        e = rng.integers(0, 3, size=(1024, W)).astype(np.uint16)
+        e[:, :3] = top
+        e[:, -2:] = top
+        e[5, W // 2] = top
+        seam, cost = sc.find_seam(_to_dev(e, dev))
+        sc.check()
+        s_ref, c_ref = oracle.dp_seam(e)
+        assert int(_np(cost)[0]) == c_ref, W
+        np.testing.assert_array_equal(_np(seam), s_ref, err_msg=f"W={W}")
+
+
 def test_carve_config2_full(dev):
     """1920x1080 -> 1440 (480 vertical seams): every seam index and every output byte."""
     job = synth.config2()
