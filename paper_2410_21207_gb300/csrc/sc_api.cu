@@ -322,8 +322,9 @@ int sc_check(void *stream) {
   if (rc) return rc;
   Workspace &ws = *wsp;
   std::lock_guard<std::mutex> lk(ws.mu);
+  // a stream with no earlier work has fresh (uninitialised) flag words: they start at zero
+  if ((rc = ensure_flags(ws, st))) return rc;
   SC_CUDA(cudaStreamSynchronize(st));
-  SC_CUDA(ws.flags.ensure(4));
   int h[2] = {0, 0};
   SC_CUDA(cudaMemcpy(h, ws.flags.p, 2 * sizeof(int), cudaMemcpyDeviceToHost));
   SC_CUDA(cudaMemset(ws.flags.p, 0, 2 * sizeof(int)));

@@ -36,3 +36,15 @@ def test_bounded_wait_times_out_and_context_survives(dev):
 def test_selftest_limit_checked(dev):
     with pytest.raises(sc.ScError):
         sc.selftest_wait_timeout(0)
+
+
+def test_check_on_fresh_streams_reports_nothing(dev):
+    """sc_check on a stream that never ran library work: its flag words are created zeroed, so
+    whatever the freshly allocated device memory held is not read as an error."""
+    junk = torch.full((1 << 22,), 0x5A, dtype=torch.uint8, device=dev)
+    del junk
+    torch.cuda.empty_cache()
+    for _ in range(4):
+        s = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(s):
+            sc.check()
