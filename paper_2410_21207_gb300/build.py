@@ -36,8 +36,12 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def _headers():
+    return glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+
+
 def _deps():
-    return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    return _sources() + _headers()
 
 
 def _stale(target: str, deps) -> bool:
@@ -51,7 +55,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile every CUDA source for sm_103a and link the library; returns its path."""
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
-    headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    headers = _headers()
     jobs = []
     objs = []
     for src in _sources():

@@ -1,4 +1,4 @@
-// Batched persistent carving with one thread-block cluster per image (images wider than a CTA).
+// Batched persistent carving with one thread-block cluster per image.
 #pragma once
 #include "sc_batch_item.h"
 
@@ -6,13 +6,36 @@ namespace sc {
 
 constexpr size_t BATCH_CL_SMEM_MAX = 232448 - 1024;   // the opt-in limit minus static shared memory
 
+// Two cluster shapes of the persistent kernel:
+//   CL_WIDE: 8 compute warps, 8-row tiles, 768 own columns per CTA. Images wider than one CTA of the
+//            one-CTA kernel: few CTAs per image, little redundant halo work (throughput).
+//   CL_LAT:  8 compute warps, 32-row tiles, 384 own columns per CTA. The heaviest images of a batch:
+//            a quarter of the tile boundaries per seam and twice the CTAs, so one image's seams
+//            finish sooner (latency), at more SM time per seam.
+enum ClShape { CL_WIDE = 0, CL_LAT = 1 };
+
+struct ClOps {
+  int own;                                                     // columns each CTA of a cluster owns
+  size_t (*smem)(int Smax);                                    // dynamic shared memory per CTA
+  cudaError_t (*capacity)(int cs, int Smax, int *clusters);    // clusters of cs CTAs resident at once
+  // `clusters` persistent clusters of cs CTAs carve items[0..n) (a queue counter at *queue, zeroed)
+  cudaError_t (*launch)(const BatchItem *items, int n, int cs, int Smax, int clusters, int *queue, int *err,
+                        cudaStream_t st);
+};
+
+ClOps cl_ops_wide();
+ClOps cl_ops_lat();
+inline ClOps cl_ops(int shape) { return shape == CL_LAT ? cl_ops_lat() : cl_ops_wide(); }
+
 // columns each CTA of the cluster owns: an image of searched width w needs ceil(w / own) CTAs
-int batch_cl_own_cols();
-size_t batch_cl_smem_bytes(int Smax);
-// clusters of cs CTAs (shared-memory plan for Smax super-tiles) resident on the GPU at once
-cudaError_t batch_cl_capacity(int cs, int Smax, int *clusters);
-// `clusters` persistent clusters of cs CTAs carve items[0..n) (a queue counter at *queue, zeroed)
-cudaError_t launch_batch_cl(const BatchItem *items, int n, int cs, int Smax, int clusters, int *queue, int *err,
-                            cudaStream_t st);
+inline int batch_cl_own_cols(int shape = CL_WIDE) { return cl_ops(shape).own; }
+inline size_t batch_cl_smem_bytes(int Smax, int shape = CL_WIDE) { return cl_ops(shape).smem(Smax); }
+inline cudaError_t batch_cl_capacity(int cs, int Smax, int *clusters, int shape = CL_WIDE) {
+  return cl_ops(shape).capacity(cs, Smax, clusters);
+}
+inline cudaError_t launch_batch_cl(const BatchItem *items, int n, int cs, int Smax, int clusters, int *queue, int *err,
+                                   cudaStream_t st, int shape = CL_WIDE) {
+  return cl_ops(shape).launch(items, n, cs, Smax, clusters, queue, err, st);
+}
 
 }  // namespace sc

@@ -109,10 +109,38 @@ namespace sc {
 // pixels left of o_q, so the q-th removal is passed exactly when j reaches it.
 constexpr int RPEND = 16;
 
-__device__ __forceinline__ int lazy_map(const int16_t *list, int m, int j) {
+// A row's pending removals in registers: the thresholds t_q = o_q - q, two 16-bit values per word,
+// from two 16-byte loads (the lists are 32-byte rows); entries q >= m get t_q = 0x7FFF, above every
+// column (columns stay below 2^15). Current column j is stored column j + #{q : t_q <= j}. A count
+// is four instructions per word: for 16-bit halves a = 0x8000 + j and b = t_q <= 0x7FFF, a - b
+// stays in [1, 0xFFFF] (no borrow between halves) and has bit 15 set exactly when t_q <= j.
+// No load per entry on the way to a pixel.
+struct LazyRow {
+  uint32_t t[RPEND / 2];
+};
+
+__device__ __forceinline__ LazyRow lazy_row(const int16_t *list, int m) {
+  const uint4 a = *reinterpret_cast<const uint4 *>(list);
+  const uint4 b = *reinterpret_cast<const uint4 *>(list + 8);
+  const uint32_t w[RPEND / 2] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  LazyRow r;
+#pragma unroll
+  for (int k = 0; k < RPEND / 2; ++k) {
+    // entries past m become 0x7FFF + q before the subtraction (o_q >= q for the others: no borrow)
+    const uint32_t lo = (2 * k < m) ? (w[k] & 0xFFFFu) : 0x7FFFu + 2 * k;
+    const uint32_t hi = (2 * k + 1 < m) ? (w[k] >> 16) : 0x7FFFu + 2 * k + 1;
+    r.t[k] = (lo | (hi << 16)) - ((uint32_t)(2 * k) | ((uint32_t)(2 * k + 1) << 16));
+  }
+  return r;
+}
+
+// removals passed by current column j (0 <= j < 2^15)
+__device__ __forceinline__ int lazy_count(const LazyRow &r, int j) {
+  const uint32_t jj = ((uint32_t)j * 0x10001u) | 0x80008000u;
   int c = 0;
-  for (int q = 0; q < m; ++q) c += ((int)list[q] - q <= j) ? 1 : 0;
-  return j + c;
+#pragma unroll
+  for (int k = 0; k < RPEND / 2; ++k) c += __popc((jj - r.t[k]) & 0x80008000u);
+  return c;
 }
 
 // The two energies of row i that the removal of `seam` changes. After deleting seam s from a
@@ -122,37 +150,71 @@ __device__ __forceinline__ int lazy_map(const int16_t *list, int m, int j) {
 // are computed from the old image seen through the removal: new pixel (r, j) = old (r, j + [j >= s_r]).
 // Returns (e(s-1) | e(s) << 16); a value is 0 when its column does not exist. *bad is set when
 // the seam column is out of range. The image is read through the pending-removal lists `lists`
-// (row r at lists + r*RPEND, m entries each) of the width-W image the seam was found in.
+// (row r at lists + r*RPEND, m entries each) of the width-W image the seam was found in; row i's
+// list comes back in *li for the insertion that follows.
 __device__ __forceinline__ uint32_t patch_row_lazy(const uint32_t *img, int pitch, int H, int W, const int32_t *seam,
-                                                   const int16_t *lists, int m, int i, bool *bad) {
+                                                   const int16_t *lists, int m, int i, bool *bad, LazyRow *li) {
   const int Wn = W - 1;
   const int s = seam[i];
+  *li = lazy_row(lists + (int64_t)i * RPEND, m);
   if (s < 0 || s >= W) {
     *bad = true;
     return 0u;
   }
-  auto pix = [&](int r, int j) -> uint32_t {
-    r = clampi(r, 0, H - 1);
+  // new pixel (r, j), j clamped to the new width, of a row r whose seam column is sr and list L
+  auto pix = [&](int r, const LazyRow &L, int sr, int j) -> uint32_t {
     j = clampi(j, 0, Wn - 1);
-    const int x = j + (j >= seam[r] ? 1 : 0);                    // column in the width-W image
-    return img[(int64_t)r * pitch + lazy_map(lists + (int64_t)r * RPEND, m, x)];
+    const int x = j + (j >= sr ? 1 : 0);                    // column in the width-W image
+    return img[(int64_t)r * pitch + x + lazy_count(L, x)];
   };
-  auto en = [&](int j) -> uint32_t { return sad4(pix(i, j + 1), pix(i, j - 1)) + sad4(pix(i + 1, j), pix(i - 1, j)); };
-  const uint32_t p0 = (s >= 1) ? en(s - 1) : 0u;
-  const uint32_t p1 = (s <= Wn - 1) ? en(s) : 0u;
+  // columns s-1 and s of the rows above and below (edge rows replicated), one row's list at a time
+  uint32_t up0, up1, dn0, dn1;
+  {
+    const int r = i > 0 ? i - 1 : 0;
+    const LazyRow L = lazy_row(lists + (int64_t)r * RPEND, m);
+    const int sr = seam[r];
+    up0 = pix(r, L, sr, s - 1);
+    up1 = pix(r, L, sr, s);
+  }
+  {
+    const int r = i + 1 < H ? i + 1 : H - 1;
+    const LazyRow L = lazy_row(lists + (int64_t)r * RPEND, m);
+    const int sr = seam[r];
+    dn0 = pix(r, L, sr, s - 1);
+    dn1 = pix(r, L, sr, s);
+  }
+  const LazyRow &lc = *li;
+  const uint32_t p0 = (s >= 1) ? sad4(pix(i, lc, s, s), pix(i, lc, s, s - 2)) + sad4(dn0, up0) : 0u;
+  const uint32_t p1 = (s <= Wn - 1) ? sad4(pix(i, lc, s, s + 1), pix(i, lc, s, s - 1)) + sad4(dn1, up1) : 0u;
   return p0 | (p1 << 16);
 }
 
-// Add row i's removal (current column s, image of the old list) to its sorted list: out gets m+1.
-__device__ __forceinline__ void list_insert(const int16_t *in, int16_t *out, int m, int s) {
-  const int o = lazy_map(in, m, s);
-  int q = 0;
-  for (; q < m && in[q] < o; ++q) out[q] = in[q];
-  out[q] = (int16_t)o;
-  for (; q < m; ++q) out[q + 1] = in[q];
+// Add a row's removal at current column s to its sorted list (L: the row's m entries): the removals
+// it passes are exactly the first c = lazy_count(s) (t_q never decreases with q), so the stored
+// column o = s + c goes in at position c. out gets m + 1 entries (two 16-byte stores).
+__device__ __forceinline__ void list_insert(const LazyRow &L, int16_t *out, int s) {
+  const int c = lazy_count(L, s);
+  const uint32_t o = (uint32_t)(s + c);
+  uint32_t raw[RPEND / 2], v[RPEND / 2];
+#pragma unroll
+  for (int k = 0; k < RPEND / 2; ++k) raw[k] = L.t[k] + ((uint32_t)(2 * k) | ((uint32_t)(2 * k + 1) << 16));   // o_q
+#pragma unroll
+  for (int k = 0; k < RPEND / 2; ++k) {
+    const uint32_t up = k > 0 ? __funnelshift_l(raw[k - 1], raw[k], 16) : (raw[0] << 16);   // entries moved up one
+    uint32_t x = 0u;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = 2 * k + h;
+      const uint32_t keep = (raw[k] >> (16 * h)) & 0xFFFFu, moved = (up >> (16 * h)) & 0xFFFFu;
+      x |= (q < c ? keep : (q == c ? o : moved)) << (16 * h);
+    }
+    v[k] = x;
+  }
+  *reinterpret_cast<uint4 *>(out) = make_uint4(v[0], v[1], v[2], v[3]);
+  *reinterpret_cast<uint4 *>(out + 8) = make_uint4(v[4], v[5], v[6], v[7]);
 }
 
-// Compact one row of stored words in place by one warp: current column j <- stored lazy_map(j), for
+// Compact one row of stored words in place by one warp: current column j <- its stored column, for
 // j < w. Sources never lie left of their destination and the row is processed left to right in
 // chunks read completely before they are written, so nothing is overwritten before it is read.
 __device__ __forceinline__ void compact_row_lazy(uint32_t *row, const int16_t *list, int m, int w, int lane) {
@@ -205,8 +267,9 @@ __device__ __forceinline__ bool refresh_row(const uint32_t *img, int pitch, uint
   shift_row_u16(er, s, W, lane, [&] {
     if (lane == 0) {
       bool bad = false;
-      p = patch_row_lazy(img, pitch, H, W, seam, lists_in, m, i, &bad);
-      list_insert(lists_in + (int64_t)i * RPEND, lists_out + (int64_t)i * RPEND, m, s);
+      LazyRow li;
+      p = patch_row_lazy(img, pitch, H, W, seam, lists_in, m, i, &bad, &li);
+      list_insert(li, lists_out + (int64_t)i * RPEND, s);
     }
   });
   if (lane == 0) {
@@ -393,17 +456,24 @@ __device__ __forceinline__ void forward_at(Pix pix, int cols, int i, int j, uint
 // other columns are shifted copies: the dirty set of the e1 refresh holds for all three planes),
 // the image read through the pending-removal lists. out[plane] = value(s-1) | value(s) << 16.
 __device__ __forceinline__ void patch_row_lazy_fwd(const uint32_t *img, int pitch, int H, int W, const int32_t *seam,
-                                                   const int16_t *lists, int m, int i, uint32_t (&out)[3], bool *bad) {
+                                                   const int16_t *lists, int m, int i, uint32_t (&out)[3], bool *bad,
+                                                   LazyRow *li) {
   const int Wn = W - 1;
-  const int s = seam[i];
+  const int iu = i > 0 ? i - 1 : 0;
+  const int s = seam[i], su = seam[iu];
+  const LazyRow lc = lazy_row(lists + (int64_t)i * RPEND, m);
+  const LazyRow lu = lazy_row(lists + (int64_t)iu * RPEND, m);
+  *li = lc;
   out[0] = out[1] = out[2] = 0u;
   if (s < 0 || s >= W) {
     *bad = true;
     return;
   }
+  // rows i (forward_at's row) and i - 1 (read only when i >= 1)
   auto pix = [&](int r, int j) -> uint32_t {
-    const int x = j + (j >= seam[r] ? 1 : 0);                    // column in the width-W image
-    return img[(int64_t)r * pitch + lazy_map(lists + (int64_t)r * RPEND, m, x)];
+    const LazyRow &L = r == i ? lc : lu;
+    const int x = j + (j >= (r == i ? s : su) ? 1 : 0);      // column in the width-W image
+    return img[(int64_t)r * pitch + x + lazy_count(L, x)];
   };
   uint32_t cu, dl, dr;
   if (s >= 1) {
@@ -425,8 +495,9 @@ __device__ __forceinline__ bool refresh_row_fwd(const uint32_t *img, int pitch, 
   uint32_t pr[3] = {0u, 0u, 0u};
   if (lane == 0) {
     bool bad = false;
-    patch_row_lazy_fwd(img, pitch, H, W, seam, lists_in, m, i, pr, &bad);
-    list_insert(lists_in + (int64_t)i * RPEND, lists_out + (int64_t)i * RPEND, m, s);
+    LazyRow li;
+    patch_row_lazy_fwd(img, pitch, H, W, seam, lists_in, m, i, pr, &bad, &li);
+    list_insert(li, lists_out + (int64_t)i * RPEND, s);
   }
 #pragma unroll
   for (int pl = 0; pl < 3; ++pl) {
