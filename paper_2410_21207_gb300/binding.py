@@ -371,7 +371,7 @@ class BatchPlan:
     def __init__(self, imgs: Sequence, targets: Sequence[Tuple[int, int]], autotune=False,
                  with_log: bool = False):
         """autotune: False/0 default configuration, True/1 time the configurations and balancing
-        variants, 2 default configuration with the heaviest images on 4-CTA clusters."""
+        variants, 2 default configuration with the heaviest images on 32-row-tile clusters."""
         torch = _torch()
         self.imgs = list(imgs)
         self.descs, self.outs, self.logs = _batch_descs(self.imgs, targets, with_log)

@@ -660,10 +660,11 @@ namespace sc {
 
 // ---- batched carve (one persistent launch; images wider than a CTA go to the cluster path) ----
 static const BatchCfg kBatchCfgs[] = {{15, 16}, {15, 8}, {12, 8}, {12, 16}, {8, 16}, {8, 8}, {8, 32}};
-// load-balancing variants the autotuner times on top of its fastest configuration: images whose
-// work exceeds thr x the mean share per SM go to clusters of 4 (higher tier) or 2 CTAs
-static const BatchCfg kBalanceCfgs[] = {{0, 0, 0, 0.f, 2, 1.0f}, {0, 0, 0, 0.f, 2, 1.6f}, {0, 0, 4, 1.6f, 0, 0.f},
-                                        {0, 0, 4, 2.0f, 2, 1.0f}};
+// load-balancing thresholds the autotuner times on top of its fastest configuration: images whose
+// work exceeds thr x the mean share per SM go to latency-shaped clusters; autotune = 2 takes
+// kBalanceDefault without timing
+static const float kBalanceThr[] = {1.0f, 1.3f, 1.6f, 2.0f, 2.5f};
+constexpr float kBalanceDefault = 1.3f;
 
 int batch_need_width(const sc_image_desc &d) {
   const int nh = d.H - d.target_h;
@@ -729,20 +730,16 @@ void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned
   size_t off = 0;
   const int limit = batch_width_limit(c.nw, c.kt);
   std::vector<int> wide;
-  // the images that would hold up the batch on one CTA each: carving work above thr x the mean
-  // share per SM goes to a cluster (the batch then ends when the average SM does, not when the
-  // largest image does)
-  std::vector<int> cs_bal(n, 1);
-  if (c.cs_hi > 1 || c.cs_lo > 1) {
+  // the images that would hold up the batch on one CTA each: carving work above thr_bal x the mean
+  // share per SM goes to a latency-shaped cluster (the batch then ends when the average SM does,
+  // not when the largest image does)
+  std::vector<char> bal(n, 0);
+  if (c.thr_bal > 0.f) {
     const int sms = device_sms();
     double total = 0.0;
     for (int k = 0; k < n; ++k) total += item_work(descs[k]);
     const double share = sms > 0 ? total / sms : 0.0;
-    for (int k = 0; k < n && share > 0.0; ++k) {
-      const double w = item_work(descs[k]);
-      if (c.cs_hi > 1 && w > share * c.thr_hi) cs_bal[k] = c.cs_hi;
-      else if (c.cs_lo > 1 && w > share * c.thr_lo) cs_bal[k] = c.cs_lo;
-    }
+    for (int k = 0; k < n && share > 0.0; ++k) bal[k] = item_work(descs[k]) > share * c.thr_bal ? 1 : 0;
   }
   for (int k = 0; k < n; ++k) {
     const sc_image_desc &d = descs[k];
@@ -750,7 +747,7 @@ void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned
     const int rows0 = (nh0 > 0 && d.target_w > d.H) ? d.target_w : d.H;
     // the refreshed pairs of a pass live in the CTA's staging ring between searches
     const size_t ring_bytes = (size_t)3 * c.kt * (c.nw * (128 - 2 * c.kt) + 2 * c.kt) * 2;
-    if (batch_need_width(d) > limit || (size_t)rows0 * 4 > ring_bytes || cs_bal[k] > 1) {
+    if (batch_need_width(d) > limit || (size_t)rows0 * 4 > ring_bytes || bal[k]) {
       wide.push_back(k);
       continue;
     }
@@ -760,21 +757,30 @@ void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned
   }
   for (int k : wide) {
     const sc_image_desc &d = descs[k];
-    const int cs = std::max(batch_cluster_size(d), cs_bal[k]);
+    int shape = CL_WIDE, cs = batch_cluster_size(d);
+    if (bal[k]) {
+      const int own = batch_cl_own_cols(CL_LAT);
+      const int cl = std::max(2, (batch_need_width(d) + own - 1) / own);
+      if (cl <= MAX_CLUSTER) {
+        shape = CL_LAT;
+        cs = cl;
+      }
+    }
     if (cs > MAX_CLUSTER) {
       b.fallback.push_back(k);
       continue;
     }
     ClusterGroup *g = nullptr;
     for (ClusterGroup &x : b.cl)
-      if (x.cs == cs) g = &x;
+      if (x.cs == cs && x.shape == shape) g = &x;
     if (!g) {
       b.cl.emplace_back();
       g = &b.cl.back();
       g->cs = cs;
+      g->shape = shape;
     }
     int S;
-    g->items.push_back(layout_item(d, cs * batch_cl_own_cols(), pool, off, &S));
+    g->items.push_back(layout_item(d, cs * batch_cl_own_cols(shape), pool, off, &S));
     g->index.push_back(k);
     if (S > g->Smax) g->Smax = S;
   }
@@ -833,18 +839,31 @@ struct BatchRun {
   BatchCfg cfg{15, 16};
   int grid = 1;
   std::vector<int> cl_clusters;   // clusters launched per group
-  // the cluster launches run beside the one-CTA launch on a second stream (fork and join events)
-  cudaStream_t side = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
+  // every cluster group runs on a stream of its own beside the one-CTA launch (fork and join
+  // events), so that the groups' persistent launches do not wait for one another
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
   BatchRun() = default;
   BatchRun(const BatchRun &) = delete;
   BatchRun &operator=(const BatchRun &) = delete;
   ~BatchRun() {
     if (fork) cudaEventDestroy(fork);
-    if (join) cudaEventDestroy(join);
-    if (side) cudaStreamDestroy(side);
+    for (cudaEvent_t e : join) cudaEventDestroy(e);
+    for (cudaStream_t x : side) cudaStreamDestroy(x);
   }
 };
+
+// carving work of a laid-out image (pixels of every searched map summed over its seams, up to a
+// constant factor)
+static double batch_item_work(const BatchItem &it) {
+  return (double)(it.W - it.tw) * it.H * it.W + (double)(it.H - it.th) * it.tw * it.H;
+}
+
+// SM time a cluster spends per unit of work, against one CTA of the one-CTA kernel: a cluster of
+// cs CTAs carves an image about cs / 2 times as fast as one CTA (measured: the largest config-4
+// image, 1254x944 -> 835, 73 ms on one CTA, 39 ms on a 4-CTA cluster of the latency shape)
+constexpr double kClusterSmCost = 2.0;
 
 // Allocates and uploads everything one batched launch needs (synchronous upload).
 static int batch_prepare(BatchRun &r, const sc_image_desc *descs, int n, const BatchCfg &c) {
@@ -864,24 +883,54 @@ static int batch_prepare(BatchRun &r, const sc_image_desc *descs, int n, const B
   SC_CUDA(cudaGetDevice(&dev));
   SC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int per_sm = batch_blocks_per_sm(c.nw, c.kt, r.setup.Smax);
+  // SMs for each cluster group in proportion to its share of the batch's SM time (one-CTA images:
+  // their work; clustered ones: kClusterSmCost x theirs), at least one cluster each and never more
+  // than resident at once or than the group has images; the one-CTA launch keeps at least one SM
   r.cl_clusters.assign(ng, 1);
+  double d1 = 0.0, dall = 0.0;
+  std::vector<double> dg(ng, 0.0);
+  for (const BatchItem &it : r.setup.items) d1 += batch_item_work(it);
+  dall = d1;
+  for (int g = 0; g < ng; ++g) {
+    for (const BatchItem &it : r.setup.cl[g].items) dg[g] += kClusterSmCost * batch_item_work(it);
+    dall += dg[g];
+  }
   int cl_sms = 0;
   for (int g = 0; g < ng; ++g) {
+    const ClusterGroup &G = r.setup.cl[g];
     int cap = 0;
-    SC_CUDA(batch_cl_capacity(r.setup.cl[g].cs, r.setup.cl[g].Smax, &cap));
-    const int ni = (int)r.setup.cl[g].items.size();
-    r.cl_clusters[g] = cap < 1 ? 1 : (cap < ni ? cap : ni);
-    cl_sms += r.cl_clusters[g] * r.setup.cl[g].cs;
+    SC_CUDA(batch_cl_capacity(G.cs, G.Smax, &cap, G.shape));
+    const int ni = (int)G.items.size();
+    int want = ni;
+    if (nb > 0 && dall > 0.0) want = (int)std::lround(sms * dg[g] / dall / G.cs);
+    want = std::max(1, std::min(want, std::min(cap < 1 ? 1 : cap, ni)));
+    r.cl_clusters[g] = want;
+    cl_sms += want * G.cs;
   }
-  // the one-CTA launch leaves the clusters' SMs to them: the two run side by side
+  // leave the one-CTA launch at least one SM: trim the groups holding the most SMs
+  while (nb > 0 && cl_sms > sms - 1) {
+    int gmax = -1;
+    for (int g = 0; g < ng; ++g)
+      if (r.cl_clusters[g] > 1 && (gmax < 0 || r.cl_clusters[g] * r.setup.cl[g].cs > r.cl_clusters[gmax] * r.setup.cl[gmax].cs))
+        gmax = g;
+    if (gmax < 0) break;
+    --r.cl_clusters[gmax];
+    cl_sms -= r.setup.cl[gmax].cs;
+  }
+  // the one-CTA launch leaves the clusters' SMs to them: they run side by side
   r.grid = (sms - (nb > 0 ? std::min(cl_sms, sms - 1) : 0)) * per_sm;
   if (r.grid > nb) r.grid = nb;
   if (r.grid < 1) r.grid = 1;
-  if (ng > 0 && nb > 0 && !r.side) {
-    SC_CUDA(cudaStreamCreateWithFlags(&r.side, cudaStreamNonBlocking));
-    SC_CUDA(cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming));
-    SC_CUDA(cudaEventCreateWithFlags(&r.join, cudaEventDisableTiming));
+  const int nside = (nb > 0 ? ng : ng - 1) > 0 ? (nb > 0 ? ng : ng - 1) : 0;   // launches beside the first
+  while ((int)r.side.size() < nside) {
+    cudaStream_t x;
+    cudaEvent_t e;
+    SC_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+    r.side.push_back(x);
+    SC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    r.join.push_back(e);
   }
+  if (nside > 0 && !r.fork) SC_CUDA(cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming));
   return SC_OK;
 }
 
@@ -891,18 +940,22 @@ static cudaError_t batch_launches(BatchRun &r, cudaStream_t st, int *err) {
   const int ng = (int)r.setup.cl.size();
   cudaError_t e = cudaMemsetAsync(r.queue.p, 0, (size_t)(1 + ng) * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  // with both kinds, the cluster launches go on the side stream and run beside the one-CTA launch
-  const bool fork = ng > 0 && nb > 0 && r.side;
-  cudaStream_t cst = fork ? r.side : st;
-  if (fork) {
+  // one launch stays on st (the one-CTA launch, else the first cluster group); every other one runs
+  // beside it on a side stream forked from st and joined back
+  const int first_side = nb > 0 ? 0 : 1;   // the first group on a side stream
+  const int nside = ng - first_side > 0 ? ng - first_side : 0;
+  if (nside > (int)r.side.size() || (nside > 0 && !r.fork)) return cudaErrorInvalidValue;
+  if (nside > 0) {
     if ((e = cudaEventRecord(r.fork, st)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(r.side, r.fork, 0)) != cudaSuccess) return e;
+    for (int q = 0; q < nside; ++q)
+      if ((e = cudaStreamWaitEvent(r.side[q], r.fork, 0)) != cudaSuccess) return e;
   }
   size_t base = nb;
   for (int g = 0; g < ng; ++g) {
     const ClusterGroup &G = r.setup.cl[g];
+    cudaStream_t cst = g >= first_side ? r.side[g - first_side] : st;
     e = launch_batch_cl(r.items.p + base, (int)G.items.size(), G.cs, G.Smax, r.cl_clusters[g], r.queue.p + 1 + g,
-                        err, cst);
+                        err, cst, G.shape);
     if (e != cudaSuccess) return e;
     base += G.items.size();
   }
@@ -910,9 +963,9 @@ static cudaError_t batch_launches(BatchRun &r, cudaStream_t st, int *err) {
     e = launch_batch(r.cfg.nw, r.cfg.kt, r.items.p, nb, r.setup.Smax, r.grid, r.queue.p, err, st);
     if (e != cudaSuccess) return e;
   }
-  if (fork) {
-    if ((e = cudaEventRecord(r.join, r.side)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(st, r.join, 0)) != cudaSuccess) return e;
+  for (int q = 0; q < nside; ++q) {
+    if ((e = cudaEventRecord(r.join[q], r.side[q])) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(st, r.join[q], 0)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -975,10 +1028,7 @@ int sc_batch_plan_create(const sc_image_desc *descs, int n, int autotune, void *
   if (!p->err) { delete p; return fail(SC_ECUDA, "cannot allocate the device error word"); }
   if (autotune < 0 || autotune > 2) { delete p; return fail(SC_EINVAL, "autotune must be 0, 1 or 2"); }
   BatchCfg best = default_batch_cfg(descs, n);
-  if (autotune == 2) {   // the default configuration with the heaviest images on 4-CTA clusters
-    best.cs_hi = 4;
-    best.thr_hi = 1.6f;
-  }
+  if (autotune == 2) best.thr_bal = kBalanceDefault;   // the default configuration, balanced
   if (autotune == 1) {
     // time every configuration that batches as many images as the default, on the real batch;
     // then, for the fastest, the load-balancing variants (the heaviest images on clusters)
@@ -1010,9 +1060,9 @@ int sc_batch_plan_create(const sc_image_desc *descs, int n, int autotune, void *
       if (ms < best_ms) { best_ms = ms; best = c; }
     }
     const BatchCfg base = best;
-    for (const BatchCfg &v : kBalanceCfgs) {
+    for (float thr : kBalanceThr) {
       BatchCfg c = base;
-      c.cs_hi = v.cs_hi; c.thr_hi = v.thr_hi; c.cs_lo = v.cs_lo; c.thr_lo = v.thr_lo;
+      c.thr_bal = thr;
       BatchSetup b;
       batch_layout(descs, n, c, nullptr, b);
       if (!b.fallback.empty() || b.cluster_images() == b0.cluster_images()) continue;   // nothing moves

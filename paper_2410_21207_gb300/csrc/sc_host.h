@@ -23,16 +23,15 @@ int static_pending_errors(int *bits);
 
 struct BatchCfg {
   int nw, kt;
-  // load balance: an image whose carving work exceeds thr x the whole batch's mean share per SM is
-  // carved by a cluster of cs CTAs instead of one CTA (cs 0: off); the higher tier is tested first
-  int cs_hi = 0;
-  float thr_hi = 0.f;
-  int cs_lo = 0;
-  float thr_lo = 0.f;
+  // load balance: an image whose carving work exceeds thr_bal x the whole batch's mean share per SM
+  // is carved by a cluster of the latency shape (CL_LAT, at least 2 CTAs) instead of one CTA, so
+  // that it does not hold up the batch (0: off)
+  float thr_bal = 0.f;
 };
-// images wider than one CTA, carved by the cluster-per-image batched kernel (one group per
-// cluster size)
+// images carved by the cluster-per-image batched kernel: those wider than one CTA (CL_WIDE
+// shape) and the heaviest ones of a balanced plan (CL_LAT); one group per shape and cluster size
 struct ClusterGroup {
+  int shape = 0;   // ClShape
   int cs = 1;
   int Smax = 1;
   std::vector<BatchItem> items;

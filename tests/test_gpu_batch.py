@@ -70,7 +70,8 @@ def test_batch_plan_autotuned_replays(dev):
     d = [torch.from_numpy(i).to(dev) for i in imgs]
     plan = sc.BatchPlan(d, targets, autotune=True, with_log=True)
     info = plan.info()
-    assert info["batched"] == len(imgs) and info["cluster_path"] == 0
+    # with idle SMs the autotuner may carve some images on latency-shaped clusters instead
+    assert info["batched"] + info["cluster_path"] == len(imgs)
     assert info["tile_rows"] in (8, 16, 32)
     for rep in range(2):
         plan.run()
@@ -125,8 +126,9 @@ def test_batch_plan_with_wide_images_replays(dev):
 
 def test_balanced_plan_runs_clusters_beside_one_cta_kernel(dev):
     """A batch dominated by one large image: with load balancing (autotune = 2) the large image is
-    carved by a 4-CTA cluster launched beside the one-CTA kernel that carves the small ones (two
-    graph branches); every image still equals the oracle's carve of it alone, on two replays."""
+    carved by a cluster of the 32-row-tile shape (1000 columns: 3 CTAs) launched beside the one-CTA
+    kernel that carves the small ones (two graph branches); every image still equals the oracle's
+    carve of it alone, on two replays."""
     big = synth.gen_image(1000, 700, 8, 20, 200, 2024)
     smalls = [synth.gen_image(120 + 9 * k, 90 + 5 * k, 3, 10, 40, 300 + k) for k in range(24)]
     imgs = [big] + smalls
@@ -135,6 +137,29 @@ def test_balanced_plan_runs_clusters_beside_one_cta_kernel(dev):
     plan = sc.BatchPlan(d, targets, autotune=2, with_log=True)
     info = plan.info()
     assert info["cluster_path"] == 1 and info["batched"] == len(smalls)
+    for _ in range(2):
+        plan.run()
+        sc.check()
+        _check(imgs, targets, plan.outs, plan.logs)
+    plan.close()
+
+
+def test_balanced_plan_several_cluster_groups(dev):
+    """Three cluster groups beside the one-CTA kernel, each on its own stream: two heavy images of
+    different widths on 32-row-tile clusters (1000 columns: 3 CTAs, 600 columns: 2 CTAs), one image
+    wider than a CTA (1700 columns) on the 8-row-tile shape, and small images on one CTA each; two
+    passes for one heavy image. Every image equals the oracle's carve of it alone, on two replays."""
+    imgs = [synth.gen_image(1000, 420, 8, 20, 200, 3031), synth.gen_image(600, 500, 6, 20, 150, 3032),
+            synth.gen_image(1700, 24, 4, 5, 20, 3033)]
+    targets = [(760, 420), (420, 460), (1696, 24)]
+    for k in range(20):
+        im = synth.gen_image(100 + 7 * k, 80 + 3 * k, 3, 10, 40, 3100 + k)
+        imgs.append(im)
+        targets.append((im.shape[1] - 5 - k % 4, im.shape[0]))
+    d = [torch.from_numpy(i).to(dev) for i in imgs]
+    plan = sc.BatchPlan(d, targets, autotune=2, with_log=True)
+    info = plan.info()
+    assert info["cluster_path"] == 3 and info["batched"] == 20
     for _ in range(2):
         plan.run()
         sc.check()
