@@ -758,7 +758,7 @@ void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned
   for (int k : wide) {
     const sc_image_desc &d = descs[k];
     int shape = CL_WIDE, cs = batch_cluster_size(d);
-    if (bal[k]) {
+    if (bal[k] || c.wide_lat) {
       const int own = batch_cl_own_cols(CL_LAT);
       const int cl = std::max(2, (batch_need_width(d) + own - 1) / own);
       if (cl <= MAX_CLUSTER) {

@@ -27,6 +27,9 @@ struct BatchCfg {
   // is carved by a cluster of the latency shape (CL_LAT, at least 2 CTAs) instead of one CTA, so
   // that it does not hold up the batch (0: off)
   float thr_bal = 0.f;
+  // images wider than one CTA take the latency shape too (where 16 CTAs of it cover them): the
+  // serving form, whose widest requests set its tail latency
+  bool wide_lat = false;
 };
 // images carved by the cluster-per-image batched kernel: those wider than one CTA (CL_WIDE
 // shape) and the heaviest ones of a balanced plan (CL_LAT); one group per shape and cluster size

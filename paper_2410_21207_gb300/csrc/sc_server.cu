@@ -134,7 +134,7 @@ struct sc_server {
   size_t budget = 0;
   int max_batch = 64;
   int dev = 0;
-  sc::BatchCfg cfg{15, 16};
+  sc::BatchCfg cfg{15, 16, 0.f, true};   // wide requests on latency-shaped clusters
   int sms = 1, occ = 1;
   sc::Arena arena;
   sc::Arena staging;                   // page-locked results of pageable output buffers (lazy)
@@ -166,11 +166,18 @@ sc_image_desc desc_of(const Request &r) {
   return d;
 }
 
-// 0 for a request one CTA carves, else the size of the cluster that carves it
+// 0 for a request one CTA carves, else the cluster that carves it: shape * 64 + cluster size (the
+// layout of a one-request batch decides both)
 int kind_of(const sc_server *s, const Request &r) {
   const sc_image_desc d = desc_of(r);
-  return batch_need_width(d) <= batch_width_limit(s->cfg.nw, s->cfg.kt) ? 0 : batch_cluster_size(d);
+  if (batch_need_width(d) <= batch_width_limit(s->cfg.nw, s->cfg.kt)) return 0;
+  BatchSetup b;
+  batch_layout(&d, 1, s->cfg, nullptr, b);
+  if (b.cl.empty()) return batch_cluster_size(d);   // wider than any cluster: refused at submission
+  return b.cl[0].shape * 64 + b.cl[0].cs;
 }
+int kind_cs(int kind) { return kind & 63; }
+int kind_shape(int kind) { return kind >> 6; }
 
 // scratch bytes and super-tiles of one request's carve
 size_t item_bytes(const sc_server *s, const sc_image_desc &d, int *S) {
@@ -249,7 +256,7 @@ bool admit(sc_server *s) {
     int S = 1;
     const size_t scratch = item_bytes(s, d, &S);
     const int sm = std::max(Smax, S);
-    const size_t smem = kind ? batch_cl_smem_bytes(sm) : batch_smem_bytes(s->cfg.nw, s->cfg.kt, sm);
+    const size_t smem = kind ? batch_cl_smem_bytes(sm, kind_shape(kind)) : batch_smem_bytes(s->cfg.nw, s->cfg.kt, sm);
     if (smem > 232448 - 1024) break;
     const size_t nin = (size_t)r.H * r.W * r.C, nout = (size_t)r.th * r.tw * r.C;
     if (s->free_flags.size() < 2) break;   // one word stays for the launch's error word
@@ -333,10 +340,10 @@ bool admit(sc_server *s) {
     auto it = s->cl_capacity.find(key);
     if (it == s->cl_capacity.end()) {
       int cap = 0;
-      if (batch_cl_capacity(kind, Smax, &cap) != cudaSuccess || cap < 1) cap = 1;
+      if (batch_cl_capacity(kind_cs(kind), Smax, &cap, kind_shape(kind)) != cudaSuccess || cap < 1) cap = 1;
       it = s->cl_capacity.emplace(key, cap).first;
     }
-    le = launch_batch_cl(dtab, n, kind, Smax, std::min(n, it->second), q, derr, G.stream);
+    le = launch_batch_cl(dtab, n, kind_cs(kind), Smax, std::min(n, it->second), q, derr, G.stream, kind_shape(kind));
   } else {
     int grid = s->sms * s->occ;
     if (grid > n) grid = n;
