@@ -1,6 +1,7 @@
 // C ABI of libsc_gb300 (declared in include/sc.h): argument checks, the per-(device, stream)
 // workspace, and the host-side seam loops of the plain path.
 #include <algorithm>
+#include <queue>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -664,7 +665,7 @@ static const BatchCfg kBatchCfgs[] = {{15, 16}, {15, 8}, {12, 8}, {12, 16}, {8, 
 // work exceeds thr x the mean share per SM go to latency-shaped clusters; autotune = 2 takes
 // kBalanceDefault without timing
 static const float kBalanceThr[] = {1.0f, 1.3f, 1.6f, 2.0f, 2.5f};
-constexpr float kBalanceDefault = 1.3f;
+constexpr float kBalanceDefault = 1.6f;
 
 int batch_need_width(const sc_image_desc &d) {
   const int nh = d.H - d.target_h;
@@ -839,19 +840,9 @@ struct BatchRun {
   BatchCfg cfg{15, 16};
   int grid = 1;
   std::vector<int> cl_clusters;   // clusters launched per group
-  // every cluster group runs on a stream of its own beside the one-CTA launch (fork and join
-  // events), so that the groups' persistent launches do not wait for one another
-  std::vector<cudaStream_t> side;
-  std::vector<cudaEvent_t> join;
-  cudaEvent_t fork = nullptr;
   BatchRun() = default;
   BatchRun(const BatchRun &) = delete;
   BatchRun &operator=(const BatchRun &) = delete;
-  ~BatchRun() {
-    if (fork) cudaEventDestroy(fork);
-    for (cudaEvent_t e : join) cudaEventDestroy(e);
-    for (cudaStream_t x : side) cudaStreamDestroy(x);
-  }
 };
 
 // carving work of a laid-out image (pixels of every searched map summed over its seams, up to a
@@ -860,10 +851,27 @@ static double batch_item_work(const BatchItem &it) {
   return (double)(it.W - it.tw) * it.H * it.W + (double)(it.H - it.th) * it.tw * it.H;
 }
 
-// SM time a cluster spends per unit of work, against one CTA of the one-CTA kernel: a cluster of
-// cs CTAs carves an image about cs / 2 times as fast as one CTA (measured: the largest config-4
-// image, 1254x944 -> 835, 73 ms on one CTA, 39 ms on a 4-CTA cluster of the latency shape)
-constexpr double kClusterSmCost = 2.0;
+// A cluster of cs CTAs carves an image in about kClusterTime / cs of one CTA's time (measured: the
+// largest config-4 image, 1254x944 -> 835, 73.4 ms on one CTA, 39.1 ms on a 4-CTA cluster of the
+// latency shape)
+constexpr double kClusterTime = 2.13;
+
+// Longest-processing-time makespan of the times t (longest first) on `slots` identical workers: how
+// a persistent launch whose queue hands out the longest carves first ends.
+static double lpt_makespan(const std::vector<double> &t, int slots) {
+  if (t.empty()) return 0.0;
+  if (slots < 1) return 1e300;
+  std::priority_queue<double, std::vector<double>, std::greater<double>> q;
+  for (int k = 0; k < slots && k < (int)t.size(); ++k) q.push(0.0);
+  double end = 0.0;
+  for (double x : t) {
+    const double f = q.top() + x;
+    q.pop();
+    q.push(f);
+    end = std::max(end, f);
+  }
+  return end;
+}
 
 // Allocates and uploads everything one batched launch needs (synchronous upload).
 static int batch_prepare(BatchRun &r, const sc_image_desc *descs, int n, const BatchCfg &c) {
@@ -883,54 +891,59 @@ static int batch_prepare(BatchRun &r, const sc_image_desc *descs, int n, const B
   SC_CUDA(cudaGetDevice(&dev));
   SC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int per_sm = batch_blocks_per_sm(c.nw, c.kt, r.setup.Smax);
-  // SMs for each cluster group in proportion to its share of the batch's SM time (one-CTA images:
-  // their work; clustered ones: kClusterSmCost x theirs), at least one cluster each and never more
-  // than resident at once or than the group has images; the one-CTA launch keeps at least one SM
+  // Clusters per group: the counts that minimise the estimated end of the batch. Each part ends as
+  // its longest-first schedule does: one-CTA images on the SMs the clusters leave (time = work,
+  // x per_sm when CTAs share an SM), a group's images on its clusters (time = work x kClusterTime /
+  // cs). For every end time T a group can reach, each group takes the fewest clusters that end by T
+  // and the one-CTA images the SMs left over; the T whose batch ends first wins. At least one
+  // cluster per group, never more than resident at once or than the group has images; the one-CTA
+  // launch keeps at least one SM.
   r.cl_clusters.assign(ng, 1);
-  double d1 = 0.0, dall = 0.0;
-  std::vector<double> dg(ng, 0.0);
-  for (const BatchItem &it : r.setup.items) d1 += batch_item_work(it);
-  dall = d1;
-  for (int g = 0; g < ng; ++g) {
-    for (const BatchItem &it : r.setup.cl[g].items) dg[g] += kClusterSmCost * batch_item_work(it);
-    dall += dg[g];
-  }
-  int cl_sms = 0;
+  std::vector<double> t1;
+  for (const BatchItem &it : r.setup.items) t1.push_back(batch_item_work(it) * per_sm);
+  std::vector<std::vector<double>> mk(ng);   // mk[g][c - 1]: group g's end on c clusters
   for (int g = 0; g < ng; ++g) {
     const ClusterGroup &G = r.setup.cl[g];
+    std::vector<double> tg;
+    for (const BatchItem &it : G.items) tg.push_back(batch_item_work(it) * kClusterTime / G.cs);
     int cap = 0;
     SC_CUDA(batch_cl_capacity(G.cs, G.Smax, &cap, G.shape));
-    const int ni = (int)G.items.size();
-    int want = ni;
-    if (nb > 0 && dall > 0.0) want = (int)std::lround(sms * dg[g] / dall / G.cs);
-    want = std::max(1, std::min(want, std::min(cap < 1 ? 1 : cap, ni)));
-    r.cl_clusters[g] = want;
-    cl_sms += want * G.cs;
+    const int lim = std::max(1, std::min(cap, (int)G.items.size()));
+    for (int q = 1; q <= lim; ++q) mk[g].push_back(lpt_makespan(tg, q));   // (items longest first)
   }
-  // leave the one-CTA launch at least one SM: trim the groups holding the most SMs
-  while (nb > 0 && cl_sms > sms - 1) {
-    int gmax = -1;
-    for (int g = 0; g < ng; ++g)
-      if (r.cl_clusters[g] > 1 && (gmax < 0 || r.cl_clusters[g] * r.setup.cl[g].cs > r.cl_clusters[gmax] * r.setup.cl[gmax].cs))
-        gmax = g;
-    if (gmax < 0) break;
-    --r.cl_clusters[gmax];
-    cl_sms -= r.setup.cl[gmax].cs;
+  if (nb == 0) {
+    for (int g = 0; g < ng; ++g) r.cl_clusters[g] = (int)mk[g].size();   // the GPU is the clusters'
+  } else if (ng > 0) {
+    double best = 1e300;
+    std::vector<int> cnt(ng);
+    for (int g0 = 0; g0 < ng; ++g0) {
+      for (double T : mk[g0]) {
+        int used = 0;
+        double e = 0.0;
+        for (int g = 0; g < ng; ++g) {
+          int q = 1;
+          while (q < (int)mk[g].size() && mk[g][q - 1] > T) ++q;
+          cnt[g] = q;
+          used += q * r.setup.cl[g].cs;
+          e = std::max(e, mk[g][q - 1]);
+        }
+        if (used > sms - 1) continue;
+        e = std::max(e, lpt_makespan(t1, (sms - used) * per_sm));
+        if (e < best) {
+          best = e;
+          r.cl_clusters = cnt;
+        }
+      }
+    }
+    // when no candidate leaves the one-CTA launch an SM, every group keeps one cluster and the
+    // launches share the GPU's SMs as they free up
   }
+  int cl_sms = 0;
+  for (int g = 0; g < ng; ++g) cl_sms += r.cl_clusters[g] * r.setup.cl[g].cs;
   // the one-CTA launch leaves the clusters' SMs to them: they run side by side
   r.grid = (sms - (nb > 0 ? std::min(cl_sms, sms - 1) : 0)) * per_sm;
   if (r.grid > nb) r.grid = nb;
   if (r.grid < 1) r.grid = 1;
-  const int nside = (nb > 0 ? ng : ng - 1) > 0 ? (nb > 0 ? ng : ng - 1) : 0;   // launches beside the first
-  while ((int)r.side.size() < nside) {
-    cudaStream_t x;
-    cudaEvent_t e;
-    SC_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
-    r.side.push_back(x);
-    SC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    r.join.push_back(e);
-  }
-  if (nside > 0 && !r.fork) SC_CUDA(cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming));
   return SC_OK;
 }
 
@@ -940,32 +953,22 @@ static cudaError_t batch_launches(BatchRun &r, cudaStream_t st, int *err) {
   const int ng = (int)r.setup.cl.size();
   cudaError_t e = cudaMemsetAsync(r.queue.p, 0, (size_t)(1 + ng) * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  // one launch stays on st (the one-CTA launch, else the first cluster group); every other one runs
-  // beside it on a side stream forked from st and joined back
-  const int first_side = nb > 0 ? 0 : 1;   // the first group on a side stream
-  const int nside = ng - first_side > 0 ? ng - first_side : 0;
-  if (nside > (int)r.side.size() || (nside > 0 && !r.fork)) return cudaErrorInvalidValue;
-  if (nside > 0) {
-    if ((e = cudaEventRecord(r.fork, st)) != cudaSuccess) return e;
-    for (int q = 0; q < nside; ++q)
-      if ((e = cudaStreamWaitEvent(r.side[q], r.fork, 0)) != cudaSuccess) return e;
-  }
+  // The launches form one chain on st: every cluster group, then the one-CTA launch, each a
+  // programmatic dependent of the one before. A cluster launch triggers its dependents as soon as
+  // every one of its CTAs is resident, so the next launch starts beside it at once and the clusters
+  // have their SMs (grouped by GPC) before the one-CTA launch spreads over the rest; each launch
+  // waits for its predecessor before it ends, so work after the chain follows all of them.
   size_t base = nb;
   for (int g = 0; g < ng; ++g) {
     const ClusterGroup &G = r.setup.cl[g];
-    cudaStream_t cst = g >= first_side ? r.side[g - first_side] : st;
     e = launch_batch_cl(r.items.p + base, (int)G.items.size(), G.cs, G.Smax, r.cl_clusters[g], r.queue.p + 1 + g,
-                        err, cst, G.shape);
+                        err, st, G.shape, g > 0);
     if (e != cudaSuccess) return e;
     base += G.items.size();
   }
   if (nb) {
-    e = launch_batch(r.cfg.nw, r.cfg.kt, r.items.p, nb, r.setup.Smax, r.grid, r.queue.p, err, st);
+    e = launch_batch(r.cfg.nw, r.cfg.kt, r.items.p, nb, r.setup.Smax, r.grid, r.queue.p, err, st, ng > 0);
     if (e != cudaSuccess) return e;
-  }
-  for (int q = 0; q < nside; ++q) {
-    if ((e = cudaEventRecord(r.join[q], r.side[q])) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(st, r.join[q], 0)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

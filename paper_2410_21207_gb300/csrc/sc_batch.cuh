@@ -173,6 +173,9 @@ __global__ void __launch_bounds__(Geo<NW, KT, false>::THREADS, 1)
     batch_carve_item<NW, KT>(cur, smem, Smax, st, err);
     __syncthreads();
   }
+  // launched as a programmatic dependent of cluster launches (a batch plan starts them first): this
+  // launch does not end before they do, so work after it on the stream follows all of them
+  pdl_wait_prerequisites();
 }
 
 constexpr size_t BATCH_SMEM_MAX = 232448 - 1024;   // the opt-in limit minus room for static shared memory
@@ -190,13 +193,22 @@ cudaError_t batch_configure_cfg() {
 
 template <int NW, int KT>
 cudaError_t launch_batch_cfg(const BatchItem *items, int n, int Smax, int grid, int *queue, int *err,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool pdl) {
   const size_t smem = search_plan<NW, KT, false, batch_fill_warps(NW, KT)>(Smax).total;
   if (smem > BATCH_SMEM_MAX) return cudaErrorInvalidValue;
   cudaError_t e = batch_configure_cfg<NW, KT>();
   if (e != cudaSuccess) return e;
-  k_batch<NW, KT><<<grid, Geo<NW, KT, false>::THREADS, smem, st>>>(items, n, Smax, queue, err);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(Geo<NW, KT, false>::THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k_batch<NW, KT>, items, n, Smax, queue, err);
 }
 
 }  // namespace sc

@@ -157,6 +157,10 @@ __global__ void __launch_bounds__(Geo<NW, KT, true, FWM>::THREADS, 1)
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int next;
   __shared__ BatchItem cur;   // the current image's descriptor, read where its fields are used
+  // a launch chained behind this one (programmatic dependent launch) may start once every CTA of
+  // this launch is resident: a batch plan places its clusters before the one-CTA launch fills the
+  // remaining SMs
+  pdl_launch_dependents();
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), cs = (int)cl.num_blocks();
   search_init<NW, KT, true, FWM>(smem, Smax);
@@ -172,6 +176,8 @@ __global__ void __launch_bounds__(Geo<NW, KT, true, FWM>::THREADS, 1)
     __syncthreads();
     clb_carve_item<NW, KT, FWM>(cur, smem, Smax, st, err, rank, cs);
   }
+  // chained behind another launch: do not end before it does (no-op otherwise)
+  pdl_wait_prerequisites();
 }
 
 // The host side of one shape: shared memory, capacity and launch (instantiated once per shape).
@@ -190,7 +196,8 @@ struct ClShapeHost {
     done.store(true);
     return cudaSuccess;
   }
-  static void cfg_for(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at, int clusters, int cs, int Smax, cudaStream_t st) {
+  static void cfg_for(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at, int clusters, int cs, int Smax, cudaStream_t st,
+                      bool pdl = false) {
     cfg = {};
     cfg.gridDim = dim3(cs * clusters);
     cfg.blockDim = dim3(G::THREADS);
@@ -200,26 +207,28 @@ struct ClShapeHost {
     at[0].val.clusterDim.x = cs;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 2 : 1;
   }
   static cudaError_t capacity(int cs, int Smax, int *clusters) {
     cudaError_t e = configure();
     if (e != cudaSuccess) return e;
     if (cs < 1 || cs > MAX_CLUSTER || smem_bytes(Smax) > BATCH_CL_SMEM_MAX) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     cfg_for(cfg, at, 1, cs, Smax, nullptr);
     return cudaOccupancyMaxActiveClusters(clusters, k_batch_cl<NW, KT, FWM>, &cfg);
   }
   static cudaError_t launch(const BatchItem *items, int n, int cs, int Smax, int clusters, int *queue, int *err,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool pdl) {
     cudaError_t e = configure();
     if (e != cudaSuccess) return e;
     if (cs < 1 || cs > MAX_CLUSTER || clusters < 1 || smem_bytes(Smax) > BATCH_CL_SMEM_MAX) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg;
-    cudaLaunchAttribute at[1];
-    cfg_for(cfg, at, clusters, cs, Smax, st);
+    cudaLaunchAttribute at[2];
+    cfg_for(cfg, at, clusters, cs, Smax, st, pdl);
     return cudaLaunchKernelEx(&cfg, k_batch_cl<NW, KT, FWM>, items, n, Smax, queue, err);
   }
   static ClOps ops() { return ClOps{G::OWC, &smem_bytes, &capacity, &launch}; }

@@ -18,9 +18,11 @@ struct ClOps {
   int own;                                                     // columns each CTA of a cluster owns
   size_t (*smem)(int Smax);                                    // dynamic shared memory per CTA
   cudaError_t (*capacity)(int cs, int Smax, int *clusters);    // clusters of cs CTAs resident at once
-  // `clusters` persistent clusters of cs CTAs carve items[0..n) (a queue counter at *queue, zeroed)
+  // `clusters` persistent clusters of cs CTAs carve items[0..n) (a queue counter at *queue, zeroed);
+  // every CTA triggers its programmatic dependents at its start; pdl: launched as a programmatic
+  // dependent of the launch before it on st, and does not end before that launch does
   cudaError_t (*launch)(const BatchItem *items, int n, int cs, int Smax, int clusters, int *queue, int *err,
-                        cudaStream_t st);
+                        cudaStream_t st, bool pdl);
 };
 
 ClOps cl_ops_wide();
@@ -34,8 +36,8 @@ inline cudaError_t batch_cl_capacity(int cs, int Smax, int *clusters, int shape 
   return cl_ops(shape).capacity(cs, Smax, clusters);
 }
 inline cudaError_t launch_batch_cl(const BatchItem *items, int n, int cs, int Smax, int clusters, int *queue, int *err,
-                                   cudaStream_t st, int shape = CL_WIDE) {
-  return cl_ops(shape).launch(items, n, cs, Smax, clusters, queue, err, st);
+                                   cudaStream_t st, int shape = CL_WIDE, bool pdl = false) {
+  return cl_ops(shape).launch(items, n, cs, Smax, clusters, queue, err, st, pdl);
 }
 
 }  // namespace sc

@@ -10,11 +10,11 @@ int batch_occ_nw8(int kt, int Smax);
 int batch_occ_nw12(int kt, int Smax);
 int batch_occ_nw15(int kt, int Smax);
 cudaError_t launch_batch_nw8(int kt, const BatchItem *items, int n, int Smax, int grid, int *queue, int *err,
-                             cudaStream_t st);
+                             cudaStream_t st, bool pdl);
 cudaError_t launch_batch_nw12(int kt, const BatchItem *items, int n, int Smax, int grid, int *queue, int *err,
-                              cudaStream_t st);
+                              cudaStream_t st, bool pdl);
 cudaError_t launch_batch_nw15(int kt, const BatchItem *items, int n, int Smax, int grid, int *queue, int *err,
-                              cudaStream_t st);
+                              cudaStream_t st, bool pdl);
 
 size_t batch_smem_bytes(int nw, int kt, int Smax) {
   return nw == 8 ? batch_smem_nw8(kt, Smax)
@@ -27,10 +27,10 @@ int batch_blocks_per_sm(int nw, int kt, int Smax) {
 }
 
 cudaError_t launch_batch(int nw, int kt, const BatchItem *items, int n, int Smax, int grid, int *queue, int *err,
-                         cudaStream_t st) {
-  if (nw == 8) return launch_batch_nw8(kt, items, n, Smax, grid, queue, err, st);
-  if (nw == 12) return launch_batch_nw12(kt, items, n, Smax, grid, queue, err, st);
-  if (nw == 15) return launch_batch_nw15(kt, items, n, Smax, grid, queue, err, st);
+                         cudaStream_t st, bool pdl) {
+  if (nw == 8) return launch_batch_nw8(kt, items, n, Smax, grid, queue, err, st, pdl);
+  if (nw == 12) return launch_batch_nw12(kt, items, n, Smax, grid, queue, err, st, pdl);
+  if (nw == 15) return launch_batch_nw15(kt, items, n, Smax, grid, queue, err, st, pdl);
   return cudaErrorInvalidValue;
 }
 

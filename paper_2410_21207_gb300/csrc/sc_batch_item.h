@@ -28,8 +28,10 @@ struct BatchItem {
 // width a CTA of nw compute warps with tile height kt covers
 inline int batch_width_limit(int nw, int kt) { return nw * (128 - 2 * kt); }
 
+// pdl: launched as a programmatic dependent of the launch before it on st (which must trigger its
+// dependents at its start); the kernel does not end before that launch does
 cudaError_t launch_batch(int nw, int kt, const BatchItem *items, int n, int Smax, int grid, int *queue, int *err,
-                         cudaStream_t st);
+                         cudaStream_t st, bool pdl = false);
 size_t batch_smem_bytes(int nw, int kt, int Smax);
 int batch_blocks_per_sm(int nw, int kt, int Smax);   // after the kernel's smem attribute is set
 
