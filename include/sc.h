@@ -268,9 +268,9 @@ int sc_carve_batch(const sc_image_desc *descs, int n, void *stream);
  * SMs first; the cluster counts minimise the estimated end of the batch.
  * autotune = 1 times every one-CTA configuration (8, 12 or 15 compute warps per CTA; DP tile
  * height 8, 16 or 32 rows) on the real batch, then load-balancing variants of the fastest (images
- * whose carving work exceeds 1.0, 1.3, 1.6, 2.0 or 2.5 x the batch's mean share per SM carved by
- * clusters of 32-row tiles, at least 2 CTAs, 384 columns per CTA), and keeps the fastest;
- * autotune = 2 takes the default configuration with that balancing at 1.6 x the mean share;
+ * whose estimated carving time exceeds 0.8, 1.0, 1.2, 1.4, 1.7 or 2.0 x the batch's mean share
+ * per SM carved by clusters of 32-row tiles, at least 2 CTAs, 384 columns per CTA), and keeps the
+ * fastest; autotune = 2 takes the default configuration with that balancing at 1.4 x the mean share;
  * 0 takes the default configuration. The images' contents may
  * change between runs; their pointers and sizes may not. sc_batch_plan_run enqueues one replay on
  * `stream`; sc_batch_plan_info reports the chosen configuration (compute warps, tile height, CTAs

@@ -664,8 +664,8 @@ static const BatchCfg kBatchCfgs[] = {{15, 16}, {15, 8}, {12, 8}, {12, 16}, {8, 
 // load-balancing thresholds the autotuner times on top of its fastest configuration: images whose
 // work exceeds thr x the mean share per SM go to latency-shaped clusters; autotune = 2 takes
 // kBalanceDefault without timing
-static const float kBalanceThr[] = {1.0f, 1.3f, 1.6f, 2.0f, 2.5f};
-constexpr float kBalanceDefault = 1.6f;
+static const float kBalanceThr[] = {0.8f, 1.0f, 1.2f, 1.4f, 1.7f, 2.0f};
+constexpr float kBalanceDefault = 1.4f;
 
 int batch_need_width(const sc_image_desc &d) {
   const int nh = d.H - d.target_h;
@@ -708,10 +708,29 @@ int batch_cluster_size(const sc_image_desc &d) {
   return (batch_need_width(d) + own - 1) / own;
 }
 
-// pixels of every searched map summed over an image's seams (the carving work)
-static double item_work(const sc_image_desc &d) {
-  const double nv = d.W - d.target_w, nh = d.H - d.target_h;
-  return nv * d.H * (d.W - (nv - 1) / 2.0) + nh * d.target_w * (d.H - (nh - 1) / 2.0);
+// Estimated carving time, for load balancing: per seam of an h-row, w-column map, c + h (a + b w)
+// microseconds, fitted to measured per-seam times of single images (one GB300, 240..1280 columns,
+// 180..944 rows): the per-row term is the chain of dependent rows, the per-column term the row's
+// work. One CTA of the one-CTA kernel: c 8.3, a 0.0874, b 9.34e-5 (a row costs as much as 936
+// columns: small images cost far more per pixel than large ones). A cluster of cs CTAs of the
+// latency shape: c 11.5, a 0.065, b 1.5e-4 / cs. The 8-row-tile cluster shape is counted as one
+// CTA on a map cs / 2 times narrower.
+struct SeamCost {
+  double c, a, b;
+};
+static SeamCost cost_one_cta() { return {8.3, 0.0874, 9.34e-5}; }
+static SeamCost cost_cluster(int shape, int cs) {
+  return shape == CL_LAT ? SeamCost{11.5, 0.065, 1.5e-4 / cs} : SeamCost{8.3, 0.0874, 9.34e-5 * 2.0 / cs};
+}
+// n seams of an h-row map whose width starts at w and drops by one per seam
+static double pass_us(const SeamCost &k, double h, double w, double n) {
+  return n * (k.c + h * k.a) + h * k.b * (n * w - n * (n - 1) / 2.0);
+}
+static double carve_us(int H, int W, int tw, int th, const SeamCost &k) {
+  return pass_us(k, H, W, W - tw) + pass_us(k, tw, H, H - th);
+}
+static double item_us(const sc_image_desc &d, const SeamCost &k) {
+  return carve_us(d.H, d.W, d.target_w, d.target_h, k);
 }
 
 static int device_sms() {
@@ -738,9 +757,9 @@ void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned
   if (c.thr_bal > 0.f) {
     const int sms = device_sms();
     double total = 0.0;
-    for (int k = 0; k < n; ++k) total += item_work(descs[k]);
+    for (int k = 0; k < n; ++k) total += item_us(descs[k], cost_one_cta());
     const double share = sms > 0 ? total / sms : 0.0;
-    for (int k = 0; k < n && share > 0.0; ++k) bal[k] = item_work(descs[k]) > share * c.thr_bal ? 1 : 0;
+    for (int k = 0; k < n && share > 0.0; ++k) bal[k] = item_us(descs[k], cost_one_cta()) > share * c.thr_bal ? 1 : 0;
   }
   for (int k = 0; k < n; ++k) {
     const sc_image_desc &d = descs[k];
@@ -788,15 +807,17 @@ void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned
   b.pool_bytes = off;
   // the queues hand out the longest carves first (longest-processing-time order), so that no
   // CTA starts a long image after the others have run dry
-  auto work = [](const BatchItem &it) {
-    return (double)(it.W - it.tw) * it.H * it.W + (double)(it.H - it.th) * it.tw * it.H;
+  auto by_time = [](const SeamCost &k) {
+    return [k](const BatchItem &a, const BatchItem &c) {
+      return carve_us(a.H, a.W, a.tw, a.th, k) > carve_us(c.H, c.W, c.tw, c.th, k);
+    };
   };
-  auto by_work = [&](const BatchItem &a, const BatchItem &c) { return work(a) > work(c); };
-  std::stable_sort(b.items.begin(), b.items.end(), by_work);
+  std::stable_sort(b.items.begin(), b.items.end(), by_time(cost_one_cta()));
   for (ClusterGroup &g : b.cl) {
+    const auto longer = by_time(cost_cluster(g.shape, g.cs));
     std::vector<int> order(g.items.size());
     for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return by_work(g.items[x], g.items[y]); });
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return longer(g.items[x], g.items[y]); });
     std::vector<BatchItem> items;
     std::vector<int> index;
     for (int q : order) {
@@ -845,16 +866,7 @@ struct BatchRun {
   BatchRun &operator=(const BatchRun &) = delete;
 };
 
-// carving work of a laid-out image (pixels of every searched map summed over its seams, up to a
-// constant factor)
-static double batch_item_work(const BatchItem &it) {
-  return (double)(it.W - it.tw) * it.H * it.W + (double)(it.H - it.th) * it.tw * it.H;
-}
-
-// A cluster of cs CTAs carves an image in about kClusterTime / cs of one CTA's time (measured: the
-// largest config-4 image, 1254x944 -> 835, 73.4 ms on one CTA, 39.1 ms on a 4-CTA cluster of the
-// latency shape)
-constexpr double kClusterTime = 2.13;
+static double batch_item_us(const BatchItem &it, const SeamCost &k) { return carve_us(it.H, it.W, it.tw, it.th, k); }
 
 // Longest-processing-time makespan of the times t (longest first) on `slots` identical workers: how
 // a persistent launch whose queue hands out the longest carves first ends.
@@ -892,20 +904,21 @@ static int batch_prepare(BatchRun &r, const sc_image_desc *descs, int n, const B
   SC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int per_sm = batch_blocks_per_sm(c.nw, c.kt, r.setup.Smax);
   // Clusters per group: the counts that minimise the estimated end of the batch. Each part ends as
-  // its longest-first schedule does: one-CTA images on the SMs the clusters leave (time = work,
-  // x per_sm when CTAs share an SM), a group's images on its clusters (time = work x kClusterTime /
-  // cs). For every end time T a group can reach, each group takes the fewest clusters that end by T
-  // and the one-CTA images the SMs left over; the T whose batch ends first wins. At least one
+  // its longest-first schedule does: one-CTA images on the SMs the clusters leave (estimated time,
+  // x per_sm when CTAs share an SM), a group's images on its clusters (estimated time on a cluster
+  // of its shape and size). For every end time T a group can reach, each group takes the fewest
+  // clusters that end by T and the one-CTA images the SMs left over; the T whose batch ends first
+  // wins. At least one
   // cluster per group, never more than resident at once or than the group has images; the one-CTA
   // launch keeps at least one SM.
   r.cl_clusters.assign(ng, 1);
   std::vector<double> t1;
-  for (const BatchItem &it : r.setup.items) t1.push_back(batch_item_work(it) * per_sm);
+  for (const BatchItem &it : r.setup.items) t1.push_back(batch_item_us(it, cost_one_cta()) * per_sm);
   std::vector<std::vector<double>> mk(ng);   // mk[g][c - 1]: group g's end on c clusters
   for (int g = 0; g < ng; ++g) {
     const ClusterGroup &G = r.setup.cl[g];
     std::vector<double> tg;
-    for (const BatchItem &it : G.items) tg.push_back(batch_item_work(it) * kClusterTime / G.cs);
+    for (const BatchItem &it : G.items) tg.push_back(batch_item_us(it, cost_cluster(G.shape, G.cs)));
     int cap = 0;
     SC_CUDA(batch_cl_capacity(G.cs, G.Smax, &cap, G.shape));
     const int lim = std::max(1, std::min(cap, (int)G.items.size()));

@@ -23,9 +23,9 @@ int static_pending_errors(int *bits);
 
 struct BatchCfg {
   int nw, kt;
-  // load balance: an image whose carving work exceeds thr_bal x the whole batch's mean share per SM
-  // is carved by a cluster of the latency shape (CL_LAT, at least 2 CTAs) instead of one CTA, so
-  // that it does not hold up the batch (0: off)
+  // load balance: an image whose estimated carving time on one CTA exceeds thr_bal x the whole
+  // batch's mean share per SM is carved by a cluster of the latency shape (CL_LAT, at least 2 CTAs)
+  // instead of one CTA, so that it does not hold up the batch (0: off)
   float thr_bal = 0.f;
   // images wider than one CTA take the latency shape too (where 16 CTAs of it cover them): the
   // serving form, whose widest requests set its tail latency
