@@ -56,6 +56,9 @@ def _args():
     ap.add_argument("--profile-batch", metavar="N", type=int, default=None,
                     help="only run the first N images of the batched workload through a batch plan twice "
                          "(for ncu captures of k_batch)")
+    ap.add_argument("--balanced", action="store_true",
+                    help="with --profile-batch: a balanced plan (autotune = 2: the heaviest images on "
+                         "latency-shaped clusters, for ncu captures of k_batch_cl)")
     ap.add_argument("--profile-search", metavar="HxW[xB]", default=None,
                     help="only call sc_find_seam a few times on a seeded HxW energy map, or sc_find_seam_multi "
                          "on B maps (for ncu captures)")
@@ -920,15 +923,15 @@ def summary(line):
     return out
 
 
-def profile_batch(n: int):
-    """The first n images of the batched workload through a batch plan (no autotuning), run twice
-    (the kernel to capture is k_batch)."""
+def profile_batch(n: int, balanced: bool = False):
+    """The first n images of the batched workload through a batch plan (no autotuning, or the
+    default balancing), run twice (the kernels to capture are k_batch and k_batch_cl)."""
     import torch
     from paper_2410_21207_gb300 import binding as sc
     from paper_2410_21207_gb300 import synth
     jobs = synth.config4()[:n]
     imgs = [torch.from_numpy(j.make()).to("cuda:0") for j in jobs]
-    plan = sc.BatchPlan(imgs, [(j.target_w, j.target_h) for j in jobs])
+    plan = sc.BatchPlan(imgs, [(j.target_w, j.target_h) for j in jobs], autotune=2 if balanced else 0)
     for _ in range(2):
         plan.run()
     torch.cuda.synchronize()
@@ -944,7 +947,7 @@ def main():
     if a.profile_search:
         return profile_search(a.profile_search)
     if a.profile_batch:
-        return profile_batch(a.profile_batch)
+        return profile_batch(a.profile_batch, a.balanced)
     if a.impl == "reference":
         return run_reference(a)
     return run_native(a)
