@@ -83,9 +83,11 @@ __device__ void batch_seam_pass(const BatchItem &it, uint32_t *words, int rows, 
     if (bad) atomicOr(err, ERR_BAD_SEAM);
     __syncthreads();
     // energy rows compacted past the seam in place, the pair at the new columns s-1 and s; the
-    // tails go through the rest of the idle ring, one buffer per warp
-    shift_rows_staged(Ecur, it.pe, rows, 0, 1, w, it.seam, pairs, warp, nwarps, lane, sbuf + (size_t)warp * sbuf_elems,
-                      sbuf_elems);
+    // tails are staged by TMA through the rest of the idle ring, one buffer per warp
+    if (!shift_rows_bulk(Ecur, it.pe, rows, 0, 1, w, it.seam, pairs, warp, nwarps, lane,
+                         reinterpret_cast<unsigned char *>(sbuf + (size_t)warp * sbuf_elems), sbuf_elems * 2) &&
+        lane == 0)
+      atomicOr(err, ERR_TIMEOUT);
     cur ^= 1;
     fence_proxy_async_global();   // the next search stages the compacted energy rows with TMA
     __syncthreads();

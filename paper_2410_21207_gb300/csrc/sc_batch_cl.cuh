@@ -64,8 +64,10 @@ __device__ void clb_seam_pass(const BatchItem &it, uint32_t *words, int rows, in
     if (bad) atomicOr(err, ERR_BAD_SEAM);
     cl.sync();
     // the owned rows' energy tails, staged through the rest of the idle ring
-    shift_rows_staged(Ecur, it.pe, nq, rank, cs, w, it.seam, pairs, warp, nwarps, lane,
-                      sbuf + (size_t)warp * sbuf_elems, sbuf_elems);
+    if (!shift_rows_bulk(Ecur, it.pe, nq, rank, cs, w, it.seam, pairs, warp, nwarps, lane,
+                         reinterpret_cast<unsigned char *>(sbuf + (size_t)warp * sbuf_elems), sbuf_elems * 2) &&
+        lane == 0)
+      atomicOr(err, ERR_TIMEOUT);
     cur ^= 1;
     if (++m == RPEND) {
       compact_rows_staged(words, it.pitch, nq, rank, cs, lb[cur], m, w - 1, warp, nwarps, lane,

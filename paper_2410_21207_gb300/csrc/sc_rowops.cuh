@@ -279,114 +279,112 @@ __device__ __forceinline__ bool refresh_row(const uint32_t *img, int pitch, uint
   return true;
 }
 
-// The energy shift of every row this warp owns, each followed by its refreshed pair. The caller's
-// rows are numbered q = 0 .. nq-1 (image row row0 + q * rstride, refreshed pair pairs[q]:
-// e(s-1) | e(s) << 16); this warp owns q = warp, warp + nwarps, ... The tails of as many rows as fit the
-// warp's shared-memory buffer (buf_elems uint16, 16-byte aligned) are copied in with cp.async, all
-// in flight at once, then written back one element to the left; eight lanes work on each row, four
-// rows at a time, so no per-row chain of dependent steps is paid row after row. Rows whose seam is
-// out of range are skipped (the caller records the error).
-__device__ inline void shift_rows_staged(uint16_t *E, int pe, int nq, int row0, int rstride, int w,
-                                         const int32_t *seam, const uint32_t *pairs, int warp, int nwarps, int lane,
-                                         uint16_t *buf, int buf_elems) {
-  const int sub = lane >> 3, sl = lane & 7;
+// The energy shift of every row this warp owns (local rows q = warp, warp + nwarps, ... of nq; image
+// row row0 + q * rstride), each followed by its refreshed pair (pairs[q]: e(s-1) | e(s) << 16), staged
+// by TMA. In rounds, the warp takes as many of its next rows as its buffer holds (a prefix sum of
+// their tail sizes over the lanes); lane l copies row l's tail (the 16-byte chunks from the one
+// holding s to the one after the new last column) with one bulk copy, all completing on one
+// mbarrier at the head of the buffer; then each row is written back one element to the left, 32
+// lanes over its chunks, reading only the staged copy (so nothing is overwritten before it is read).
+// buf: this warp's buffer, 16-byte aligned, buf_bytes of it (the first 16 hold the mbarrier). Rows
+// whose seam is out of range are skipped (the caller records the error). Returns false when a wait
+// ran out (the caller records ERR_TIMEOUT).
+__device__ inline bool shift_rows_bulk(uint16_t *E, int pe, int nq, int row0, int rstride, int w, const int32_t *seam,
+                                       const uint32_t *pairs, int warp, int nwarps, int lane, unsigned char *buf,
+                                       int buf_bytes) {
+  uint64_t *bar = reinterpret_cast<uint64_t *>(buf);
+  unsigned char *data = buf + 16;
+  const int cap = buf_bytes - 16;
   const int c_last = (w - 2) >> 3;   // the chunk holding the new last column
-  // the warp's rows in blocks of 32: one seam load per lane, read back with shuffles
-  for (int blk = warp; blk < nq; blk += 32 * nwarps) {
-    const int my_q = blk + lane * nwarps;
-    const int my_s = my_q < nq ? seam[row0 + my_q * rstride] : -1;
-    const int nb = min(32, (nq - blk + nwarps - 1) / nwarps);
-    int k = 0;
-    while (k < nb) {
-      // a group of rows whose tails fit the buffer; lane q records group row q (block index, offset)
-      int info_k = 0, info_off = 0, ng = 0, used = 0;
-      while (k < nb) {
-        const int i = blk + k * nwarps;   // local row: image row row0 + i * rstride
-        const int s = __shfl_sync(0xffffffffu, my_s, k);
-        if (s < 0 || s >= w) { ++k; continue; }
-        uint16_t *er = E + (size_t)(row0 + i * rstride) * pe;
-        if (s >= w - 1) {   // nothing to shift: only the left refreshed value
-          if (lane == 0 && s >= 1) er[s - 1] = (uint16_t)(pairs[i] & 0xFFFFu);
-          ++k;
-          continue;
-        }
-        const int need = 8 * (c_last - (s >> 3) + 2);   // the tail's chunks, plus the one after it
-        if (need > buf_elems) {   // a tail longer than the buffer: shifted in place, chunk by chunk
-          if (ng > 0) break;
-          shift_row_u16(er, s, w, lane);
-          __syncwarp();
-          if (lane == 0) {
-            if (s >= 1) er[s - 1] = (uint16_t)(pairs[i] & 0xFFFFu);
-            er[s] = (uint16_t)(pairs[i] >> 16);
-          }
-          ++k;
-          continue;
-        }
-        if (ng == 32 || used + need > buf_elems) break;
-        if (lane == ng) {
-          info_k = k;
-          info_off = used;
-        }
-        used += need;
-        ++ng;
-        ++k;
-      }
-      // copy in: eight lanes per row, four rows at a time
-      for (int q0 = 0; q0 < ng; q0 += 4) {
-        const int q = q0 + sub, qq = q < ng ? q : ng - 1;
-        const int kk = __shfl_sync(0xffffffffu, info_k, qq);
-        const int off = __shfl_sync(0xffffffffu, info_off, qq);
-        const int s = __shfl_sync(0xffffffffu, my_s, kk);
-        if (q < ng) {
-          const uint16_t *er = E + (size_t)(row0 + (blk + kk * nwarps) * rstride) * pe;
-          const int c_lo = s >> 3, nch = c_last - c_lo + 2;
-          for (int c = sl; c < nch; c += 8) cp_async16(buf + off + 8 * c, er + 8 * (c_lo + c));
-        }
-      }
-      cp_async_wait_all();
-      __syncwarp();
-      // write back shifted, the first chunk keeping its elements left of s, then the refreshed pair
-      for (int q0 = 0; q0 < ng; q0 += 4) {
-        const int q = q0 + sub, qq = q < ng ? q : ng - 1;
-        const int kk = __shfl_sync(0xffffffffu, info_k, qq);
-        const int off = __shfl_sync(0xffffffffu, info_off, qq);
-        const int s = __shfl_sync(0xffffffffu, my_s, kk);
-        if (q < ng) {
-          const int r = blk + kk * nwarps;
-          uint16_t *er = E + (size_t)(row0 + r * rstride) * pe;
-          const uint16_t *b = buf + off;
-          const int c_lo = s >> 3;
-          for (int c = c_lo + sl; c <= c_last; c += 8) {
-            const uint4 x = *reinterpret_cast<const uint4 *>(b + 8 * (c - c_lo));
-            const uint32_t nx = b[8 * (c - c_lo) + 8];
-            uint4 o;
-            o.x = __funnelshift_r(x.x, x.y, 16);
-            o.y = __funnelshift_r(x.y, x.z, 16);
-            o.z = __funnelshift_r(x.z, x.w, 16);
-            o.w = __funnelshift_r(x.w, nx, 16);
-            if (c == c_lo) {
-              const int keep = s - 8 * c;   // leading elements of this chunk that stay
-              auto merge = [keep](uint32_t in, uint32_t sh, int j) {
-                const uint32_t m = (2 * j < keep ? 0x0000FFFFu : 0u) | (2 * j + 1 < keep ? 0xFFFF0000u : 0u);
-                return (in & m) | (sh & ~m);
-              };
-              o.x = merge(x.x, o.x, 0);
-              o.y = merge(x.y, o.y, 1);
-              o.z = merge(x.z, o.z, 2);
-              o.w = merge(x.w, o.w, 3);
-            }
-            *reinterpret_cast<uint4 *>(er + 8 * c) = o;
-            if (c == c_lo) {   // this lane wrote the chunk holding s: the refreshed pair goes over it
-              const uint32_t pr = pairs[r];
-              if (s >= 1) er[s - 1] = (uint16_t)(pr & 0xFFFFu);
-              if (s <= w - 2) er[s] = (uint16_t)(pr >> 16);
-            }
-          }
-        }
-      }
-      __syncwarp();   // the buffer is reused by the next group
+  const int nk = warp < nq ? (nq - warp + nwarps - 1) / nwarps : 0;
+  if (nk == 0) return true;
+  if (lane == 0) mbar_init(bar, 1);
+  fence_mbar_init();
+  __syncwarp();
+  uint32_t parity = 0;
+  bool ok = true;
+  for (int k0 = 0; k0 < nk;) {
+    const int k = k0 + lane;
+    const int q = warp + k * nwarps;
+    const int s = k < nk ? seam[row0 + q * rstride] : -1;
+    uint16_t *er = E + (size_t)(row0 + (k < nk ? q : 0) * rstride) * pe;
+    const int bytes = (k < nk && s >= 0 && s < w - 1) ? 16 * (c_last - (s >> 3) + 2) : 0;
+    int incl = bytes;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += t;
     }
+    // the rows taken are a prefix of the lanes (incl never decreases)
+    const int n = __popc(__ballot_sync(0xffffffffu, k < nk && incl <= cap));
+    if (n == 0) {   // the next row's tail alone exceeds the buffer: shifted in place, chunk by chunk
+      const int s0 = __shfl_sync(0xffffffffu, s, 0);
+      uint16_t *e0 = E + (size_t)(row0 + warp * rstride + k0 * nwarps * rstride) * pe;
+      const uint32_t pr = pairs[warp + k0 * nwarps];
+      shift_row_u16(e0, s0, w, lane);
+      __syncwarp();
+      if (lane == 0) {
+        if (s0 >= 1) e0[s0 - 1] = (uint16_t)(pr & 0xFFFFu);
+        e0[s0] = (uint16_t)(pr >> 16);
+      }
+      k0 += 1;
+      continue;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, n - 1);
+    const int off = incl - bytes;
+    if (total > 0) {
+      fence_proxy_async_smem();   // this warp's reads of the buffer's previous round come first
+      __syncwarp();
+      if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)total);
+      __syncwarp();
+      if (lane < n && bytes > 0) bulk_g2s(data + off, er + 8 * (s >> 3), (uint32_t)bytes, bar);
+      ok = mbar_wait_bounded(bar, parity, WAIT_TIMEOUT_NS);
+      parity ^= 1u;
+      if (!__all_sync(0xffffffffu, ok)) return false;   // copies may be in flight: the barrier stays
+    }
+    // a seam in the last column: nothing to shift, only the left refreshed value
+    if (lane < n && s == w - 1 && s >= 1) er[s - 1] = (uint16_t)(pairs[q] & 0xFFFFu);
+    for (int t = 0; t < n; ++t) {
+      const int bt = __shfl_sync(0xffffffffu, bytes, t);
+      if (bt == 0) continue;
+      const int st = __shfl_sync(0xffffffffu, s, t), ot = __shfl_sync(0xffffffffu, off, t);
+      const int qt = warp + (k0 + t) * nwarps;
+      uint16_t *et = E + (size_t)(row0 + qt * rstride) * pe;
+      const uint16_t *b = reinterpret_cast<const uint16_t *>(data + ot);
+      const int c_lo = st >> 3;
+      for (int c = c_lo + lane; c <= c_last; c += 32) {
+        const uint4 x = *reinterpret_cast<const uint4 *>(b + 8 * (c - c_lo));
+        const uint32_t nx = b[8 * (c - c_lo) + 8];
+        uint4 o;
+        o.x = __funnelshift_r(x.x, x.y, 16);
+        o.y = __funnelshift_r(x.y, x.z, 16);
+        o.z = __funnelshift_r(x.z, x.w, 16);
+        o.w = __funnelshift_r(x.w, nx, 16);
+        if (c == c_lo) {
+          const int keep = st - 8 * c;   // leading elements of this chunk that stay
+          auto merge = [keep](uint32_t in, uint32_t sh, int j) {
+            const uint32_t m = (2 * j < keep ? 0x0000FFFFu : 0u) | (2 * j + 1 < keep ? 0xFFFF0000u : 0u);
+            return (in & m) | (sh & ~m);
+          };
+          o.x = merge(x.x, o.x, 0);
+          o.y = merge(x.y, o.y, 1);
+          o.z = merge(x.z, o.z, 2);
+          o.w = merge(x.w, o.w, 3);
+        }
+        *reinterpret_cast<uint4 *>(et + 8 * c) = o;
+        if (c == c_lo) {   // this lane wrote the chunk holding s: the refreshed pair goes over it
+          const uint32_t pr = pairs[qt];
+          if (st >= 1) et[st - 1] = (uint16_t)(pr & 0xFFFFu);
+          et[st] = (uint16_t)(pr >> 16);
+        }
+      }
+    }
+    __syncwarp();   // the buffer is reused by the next round
+    k0 += n;
   }
+  __syncwarp();
+  if (lane == 0) mbar_inval(bar);   // the buffer holds other data next
+  return ok;
 }
 
 // compact_row_lazy for every row this warp owns (local rows q = warp, warp + nwarps, ... of nq;
