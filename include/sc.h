@@ -286,8 +286,9 @@ int sc_batch_plan_destroy(sc_batch_plan *plan);
  * A worker thread admits queued requests whenever the arena and a stream have room, as
  * micro-batches of up to max_batch requests of one kind, in arrival order within the kind:
  * requests that fit one CTA (searched width <= 1440) go to one persistent one-CTA-per-image
- * launch, wider ones to one persistent cluster-per-image launch per cluster size (clusters of
- * 32-row tiles, 384 columns per CTA: the widest requests set the tail latency). Micro-batches
+ * launch, wider ones, and those whose carve on one CTA would take over an estimated 50 ms, to one
+ * persistent cluster-per-image launch per cluster size (clusters of 32-row tiles, 384 columns per
+ * CTA: the heaviest requests set the tail latency). Micro-batches
  * on different streams run concurrently, so requests submitted while others are on the GPU start
  * as soon as memory and a stream free up. Every result equals sc_carve of that image alone.
  * sc_server_submit: img_host (H*W*C bytes) and out_host (target_h*target_w*C bytes) are host

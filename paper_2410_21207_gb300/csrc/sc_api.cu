@@ -761,6 +761,9 @@ void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned
     const double share = sms > 0 ? total / sms : 0.0;
     for (int k = 0; k < n && share > 0.0; ++k) bal[k] = item_us(descs[k], cost_one_cta()) > share * c.thr_bal ? 1 : 0;
   }
+  if (c.lat_us > 0.f)
+    for (int k = 0; k < n; ++k)
+      if (item_us(descs[k], cost_one_cta()) > c.lat_us) bal[k] = 1;
   for (int k = 0; k < n; ++k) {
     const sc_image_desc &d = descs[k];
     const int nh0 = d.H - d.target_h;

@@ -30,6 +30,9 @@ struct BatchCfg {
   // images wider than one CTA take the latency shape too (where 16 CTAs of it cover them): the
   // serving form, whose widest requests set its tail latency
   bool wide_lat = false;
+  // images whose estimated carving time on one CTA exceeds lat_us microseconds take the latency
+  // shape as well (0: off): the serving form's heaviest narrow requests
+  float lat_us = 0.f;
 };
 // images carved by the cluster-per-image batched kernel: those wider than one CTA (CL_WIDE
 // shape) and the heaviest ones of a balanced plan (CL_LAT); one group per shape and cluster size

@@ -6,8 +6,9 @@
 //   2. admits queued requests while the device-memory ledger (one arena of the configured budget,
 //      first-fit) has room, as micro-batches of up to max_batch requests of one kind, in arrival
 //      order within the kind: requests that fit one CTA go to the one-CTA persistent kernel
-//      (k_batch), wider ones to the cluster-per-image persistent kernel (k_batch_cl), one
-//      micro-batch per cluster size,
+//      (k_batch), wider ones and those whose one-CTA carve would take over an estimated 50 ms to
+//      the cluster-per-image persistent kernel in its latency shape (k_batch_cl), one micro-batch
+//      per cluster size,
 //   3. enqueues each micro-batch on a free stream: host->device copies of the inputs, the launch,
 //      a completion event.
 // The kernels write every carved image straight into host memory (the caller's page-locked output
@@ -134,7 +135,8 @@ struct sc_server {
   size_t budget = 0;
   int max_batch = 64;
   int dev = 0;
-  sc::BatchCfg cfg{15, 16, 0.f, true};   // wide requests on latency-shaped clusters
+  // wide requests, and those whose one-CTA carve would take over 50 ms, on latency-shaped clusters
+  sc::BatchCfg cfg{15, 16, 0.f, true, 50000.f};
   int sms = 1, occ = 1;
   sc::Arena arena;
   sc::Arena staging;                   // page-locked results of pageable output buffers (lazy)
@@ -170,9 +172,9 @@ sc_image_desc desc_of(const Request &r) {
 // layout of a one-request batch decides both)
 int kind_of(const sc_server *s, const Request &r) {
   const sc_image_desc d = desc_of(r);
-  if (batch_need_width(d) <= batch_width_limit(s->cfg.nw, s->cfg.kt)) return 0;
   BatchSetup b;
   batch_layout(&d, 1, s->cfg, nullptr, b);
+  if (!b.items.empty()) return 0;
   if (b.cl.empty()) return batch_cluster_size(d);   // wider than any cluster: refused at submission
   return b.cl[0].shape * 64 + b.cl[0].cs;
 }
