@@ -73,14 +73,9 @@ __device__ void batch_seam_pass(const BatchItem &it, uint32_t *words, int rows, 
     a.gated = false;
     seam_search<NW, KT, false, batch_fill_warps(NW, KT)>(a, smem, Smax, st);   // ends with a CTA barrier: the seam is complete
     // every row's refreshed pair and list update, one thread per row (into the idle staging ring)
-    bool bad = false;
-#pragma unroll 1
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-      LazyRow li;
-      pairs[i] = patch_row_lazy(words, it.pitch, rows, w, it.seam, lb[cur], m, i, &bad, &li);
-      if (!bad) list_insert(li, lb[cur ^ 1] + (size_t)i * RPEND, it.seam[i]);
-    }
-    if (bad) atomicOr(err, ERR_BAD_SEAM);
+    if (refresh_pairs(words, it.pitch, rows, w, it.seam, lb[cur], lb[cur ^ 1], m, rows, 0, 1, pairs, threadIdx.x,
+                      blockDim.x))
+      atomicOr(err, ERR_BAD_SEAM);
     __syncthreads();
     // energy rows compacted past the seam in place, the pair at the new columns s-1 and s; the
     // tails are staged by TMA through the rest of the idle ring, one buffer per warp

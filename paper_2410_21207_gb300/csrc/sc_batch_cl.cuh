@@ -53,15 +53,9 @@ __device__ void clb_seam_pass(const BatchItem &it, uint32_t *words, int rows, in
     a.err = err;
     a.gated = false;
     seam_search<NW, KT, true, FWM>(a, smem, Smax, st);   // ends with a cluster barrier
-    bool bad = false;
-#pragma unroll 1
-    for (int q = threadIdx.x; rank + q * cs < rows; q += blockDim.x) {
-      const int i = rank + q * cs;
-      LazyRow li;
-      pairs[q] = patch_row_lazy(words, it.pitch, rows, w, it.seam, lb[cur], m, i, &bad, &li);
-      if (!bad) list_insert(li, lb[cur ^ 1] + (size_t)i * RPEND, it.seam[i]);
-    }
-    if (bad) atomicOr(err, ERR_BAD_SEAM);
+    if (refresh_pairs(words, it.pitch, rows, w, it.seam, lb[cur], lb[cur ^ 1], m, nq, rank, cs, pairs, threadIdx.x,
+                      blockDim.x))
+      atomicOr(err, ERR_BAD_SEAM);
     cl.sync();
     // the owned rows' energy tails, staged through the rest of the idle ring
     if (!shift_rows_bulk(Ecur, it.pe, nq, rank, cs, w, it.seam, pairs, warp, nwarps, lane,

@@ -214,6 +214,24 @@ __device__ __forceinline__ void list_insert(const LazyRow &L, int16_t *out, int 
   *reinterpret_cast<uint4 *>(out + 8) = make_uint4(v[4], v[5], v[6], v[7]);
 }
 
+// The refreshed pairs and pending-removal list updates of the rows one thread handles (local rows
+// q = t0, t0 + tstride, ... of nq; image row row0 + q * rstride): pairs[q] gets row q's pair (as
+// patch_row_lazy) and lists_out its list with this seam's removal added. Returns true when a seam
+// column was out of range (the rows after it are left alone).
+__device__ __forceinline__ bool refresh_pairs(const uint32_t *img, int pitch, int H, int W, const int32_t *seam,
+                                           const int16_t *lists_in, int16_t *lists_out, int m, int nq, int row0,
+                                           int rstride, uint32_t *pairs, int t0, int tstride) {
+  bool bad = false;
+#pragma unroll 1
+  for (int q = t0; q < nq; q += tstride) {
+    const int i = row0 + q * rstride;
+    LazyRow li;
+    pairs[q] = patch_row_lazy(img, pitch, H, W, seam, lists_in, m, i, &bad, &li);
+    if (!bad) list_insert(li, lists_out + (size_t)i * RPEND, seam[i]);
+  }
+  return bad;
+}
+
 // Compact one row of stored words in place by one warp: current column j <- its stored column, for
 // j < w. Sources never lie left of their destination and the row is processed left to right in
 // chunks read completely before they are written, so nothing is overwritten before it is read.
@@ -288,8 +306,10 @@ __device__ __forceinline__ bool refresh_row(const uint32_t *img, int pitch, uint
 // lanes over its chunks, reading only the staged copy (so nothing is overwritten before it is read).
 // buf: this warp's buffer, 16-byte aligned, buf_bytes of it (the first 16 hold the mbarrier). Rows
 // whose seam is out of range are skipped (the caller records the error). Returns false when a wait
-// ran out (the caller records ERR_TIMEOUT).
-__device__ inline bool shift_rows_bulk(uint16_t *E, int pe, int nq, int row0, int rstride, int w, const int32_t *seam,
+// ran out (the caller records ERR_TIMEOUT). Not inlined (nor is compact_rows_staged): a separate
+// function gets its own register allocation, and inlined the two phases cost the one-CTA batched
+// kernel ~160 bytes of spills.
+static __device__ __noinline__ bool shift_rows_bulk(uint16_t *E, int pe, int nq, int row0, int rstride, int w, const int32_t *seam,
                                        const uint32_t *pairs, int warp, int nwarps, int lane, unsigned char *buf,
                                        int buf_bytes) {
   uint64_t *bar = reinterpret_cast<uint64_t *>(buf);
@@ -393,7 +413,7 @@ __device__ inline bool shift_rows_bulk(uint16_t *E, int pe, int nq, int row0, in
 // output word is gathered from the buffer. The removals are held one per lane (o_q - q in lane q);
 // for 32 consecutive outputs one ballot counts those left of the first and a second finds the few
 // that fall inside, instead of comparing every output with every removal.
-__device__ inline void compact_rows_staged(uint32_t *img, int pitch, int nq, int row0, int rstride,
+static __device__ __noinline__ void compact_rows_staged(uint32_t *img, int pitch, int nq, int row0, int rstride,
                                            const int16_t *lists, int m, int w, int warp, int nwarps, int lane,
                                            uint32_t *buf, int buf_words) {
   const int piece = ((buf_words - 24) / 32) * 32;   // outputs per staged piece
