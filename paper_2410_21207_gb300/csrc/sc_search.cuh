@@ -321,6 +321,224 @@ __device__ __forceinline__ void group_sync() {
 
 // The search. Every thread of the CTA (of every CTA of the cluster when CL) calls it with the same
 // arguments; `Smax` is the super-tile count the shared-memory plan was sized for.
+// The parallel backtrack of seam_search: each fill warp recomputes its super-tiles (rows s*KSS ..
+// s*KSS+KSS-1, s = warp*cs + rank, + FW*cs, ...) in a FILLW-column window from the saved cost row
+// above them, with explicit directions, and walks them up from the chain's column at the bottom.
+// A path cell r rows into a super-tile lies within KSS - 1 - r columns of the bottom column jb[s],
+// and its three predecessors depend on the saved row only within KSS columns of jb[s]: the window
+// [x0, x0 + FILLW) with x0 = jb[s] - FILLW / 2 (rounded down to FV) holds them all. Energies are
+// read in chunks of CH rows, the next chunk loaded ahead of the current one's rows.
+struct FillCtx {
+  const uint16_t *E;
+  const uint32_t *Mrow;
+  const int *jb0;      // the chain's columns (rank 0's jb)
+  uint16_t *fdir;      // direction rows of the fill warps
+  int32_t *seam, *seam_log;
+  int *err;
+  int64_t pstride;
+  int pitch_e, pitch_m, H, W, Wa, S, rank, cs;
+  uint32_t best_m;     // the argmin's cost, checked against the recomputed one
+};
+
+template <int NW, int KT, bool CL, int FWM, bool FWD, int KSS, bool DIRECT, int CH>
+__device__ __forceinline__ void backtrack_fill(const FillCtx &f, int warp, int lane) {
+  using G = Geo<NW, KT, CL, FWM, KSS>;
+  constexpr int NP = FWD ? 3 : 1;   // cost planes per row
+  constexpr int FV = G::FV, FILLW = G::FILLW;
+  // direction rows: 2 bits per column (FV = 8), or one byte per column (FV = 4: the walk then
+  // reads its column's byte directly)
+  using DirT = typename std::conditional<FV == 8, uint16_t, uint32_t>::type;
+  using EVec = typename std::conditional<FV == 8, uint4, uint2>::type;        // FV uint16 energies
+  constexpr int PST = 32 * (int)sizeof(DirT) / 4;   // 32-bit words per direction row
+  DirT *fd = reinterpret_cast<DirT *>(f.fdir) + (size_t)warp * KSS * 32;
+  const uint16_t *const Ef = f.E;
+  int32_t *const seam_out = f.seam;
+  int32_t *const seam_log = f.seam_log;
+  int *const errw = f.err;
+  const uint32_t *const Mrow = f.Mrow;
+  const int *const jb0 = f.jb0;
+  const int64_t pstride = f.pstride;
+  const int pitch_e = f.pitch_e, pitch_m = f.pitch_m, H = f.H, W = f.W, Wa = f.Wa, S = f.S, rank = f.rank, cs = f.cs;
+  const uint32_t best_m = f.best_m;
+  // the energies of a super-tile's window (KSS rows, two rows per lane at most) are prefetched
+  // into L2 one super-tile ahead: the map has usually left L2 since the DP pass read it. The
+  // prefetch starts on a 16-byte boundary and covers the window.
+  auto prefetch_window = [&](int s) {
+    if (s >= S) return;
+    int x0 = jb0[s] - FILLW / 2;
+    x0 -= ((x0 % 8) + 8) % 8;
+    int x1 = x0 + FILLW + 8;
+    if (DIRECT) {   // only the caller's columns
+      x0 = max(x0, 0);
+      x1 = min(x1, Wa);
+      if (x1 <= x0) return;
+    }
+    for (int i = s * KSS + lane; i < s * KSS + KSS && i < H; i += 32)
+#pragma unroll
+      for (int pl = 0; pl < NP; ++pl)
+        bulk_prefetch_l2(Ef + pl * pstride + (size_t)i * pitch_e + x0, (uint32_t)(x1 - x0) * 2);
+  };
+  auto unpack = [](const EVec &v, uint32_t (&x)[FV]) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(&v);
+#pragma unroll
+    for (int q = 0; q < FV / 2; ++q) {
+      x[2 * q] = w[q] & 0xFFFFu;
+      x[2 * q + 1] = w[q] >> 16;
+    }
+  };
+  prefetch_window(warp * cs + rank);
+  for (int s = warp * cs + rank; s < S; s += G::FW * cs) {
+    prefetch_window(s + G::FW * cs);
+    const int jbs = jb0[s];
+    const int jprev = (s > 0) ? jb0[s - 1] : jb0[S];
+    int x0 = jbs - FILLW / 2;
+    x0 -= ((x0 % FV) + FV) % FV;
+    const int xc = x0 + lane * FV;
+    const int rs = s * KSS, re = (rs + KSS < H) ? rs + KSS : H;
+    const int first = (s == 0) ? 1 : rs;
+    uint32_t m[FV], oob[FV];
+#pragma unroll
+    for (int u = 0; u < FV; ++u) oob[u] = (xc + u < 0 || xc + u >= W) ? SENT : 0u;
+    // DIRECT: a lane's FV columns lie wholly inside or wholly outside the caller's [0, Wa)
+    const bool xin = !DIRECT || (xc >= 0 && xc + FV <= Wa);
+    if (s == 0) {
+      EVec v0{};
+      if (xin) v0 = *reinterpret_cast<const EVec *>(Ef + xc);
+      unpack(v0, m);
+    } else {
+#pragma unroll
+      for (int q = 0; q < FV / 4; ++q) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(Mrow + (size_t)s * pitch_m + xc + 4 * q);
+        m[4 * q] = a.x; m[4 * q + 1] = a.y; m[4 * q + 2] = a.z; m[4 * q + 3] = a.w;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < FV; ++u) m[u] |= oob[u];
+    // rows first..re-1 in chunks of CH rows, the next chunk's energies loaded ahead
+    EVec eb0[NP][CH], eb1[NP][CH];
+    auto load_chunk = [&](EVec (&eb)[NP][CH], int rbeg) {
+#pragma unroll
+      for (int r = 0; r < CH; ++r) {
+        const int i = rbeg + r;
+#pragma unroll
+        for (int pl = 0; pl < NP; ++pl)
+          if (i < re) {
+            if (xin) eb[pl][r] = *reinterpret_cast<const EVec *>(Ef + pl * pstride + (size_t)i * pitch_e + xc);
+            else eb[pl][r] = EVec{};
+          }
+      }
+    };
+    auto run_chunk = [&](const EVec (&eb)[NP][CH], int rbeg) {
+#pragma unroll
+      for (int r = 0; r < CH; ++r) {
+        const int i = rbeg + r;
+        if (i >= re) break;
+        uint32_t ee[FV], dl[FV], dr[FV];
+#pragma unroll
+        for (int u = 0; u < FV; ++u) dl[u] = dr[u] = 0u;
+        unpack(eb[0][r], ee);
+        if (FWD) {
+          unpack(eb[NP > 1 ? 1 : 0][r], dl);
+          unpack(eb[NP > 2 ? 2 : 0][r], dr);
+        }
+        const uint32_t L = __shfl_up_sync(0xffffffffu, m[FV - 1], 1);
+        const uint32_t R = __shfl_down_sync(0xffffffffu, m[0], 1);
+        uint32_t nm[FV];
+        uint32_t dirs = 0;
+#pragma unroll
+        for (int u = 0; u < FV; ++u) {
+          const uint32_t a = ((u == 0) ? L : m[u - 1]) + dl[u];
+          const uint32_t b = m[u];
+          const uint32_t c = ((u == FV - 1) ? R : m[u + 1]) + dr[u];
+          const uint32_t mn = min3u(a, b, c);
+          const uint32_t dd = (a == mn) ? 0u : ((b == mn) ? 1u : 2u);
+          dirs |= dd << ((FV == 4 ? 8 : 2) * u);
+          nm[u] = add_mask<true>(mn, ee[u], oob[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < FV; ++u) m[u] = nm[u];
+        fd[(i - rs) * 32 + lane] = (DirT)dirs;
+      }
+    };
+    int rb = first;
+    load_chunk(eb0, rb);
+    while (rb < re) {
+      if (rb + CH < re) load_chunk(eb1, rb + CH);
+      run_chunk(eb0, rb);
+      rb += CH;
+      if (rb >= re) break;
+      if (rb + CH < re) load_chunk(eb0, rb + CH);
+      run_chunk(eb1, rb);
+      rb += CH;
+    }
+    if (s == S - 1) {
+      // the recomputed cost at the bottom of the seam must be the argmin's
+      const int rel = jbs - x0;
+      if (rel / FV == lane) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int u = 0; u < FV; ++u) if (u == rel % FV) v = m[u];
+        if (v != best_m) atomicOr(errw, ERR_COST_MISMATCH);
+      }
+    }
+    __syncwarp();
+    // lane 0 follows the directions up the window (relative columns, kept in the direction rows it
+    // has read: a row's entry is not needed again), then the warp writes the seam rows
+    uint32_t *path = reinterpret_cast<uint32_t *>(fd);   // path[(i - rs) * PST] holds the column of row i
+    if (lane == 0) {
+      int rel = jbs - x0;
+      bool okp = true;
+      if constexpr (FV == 4) {
+        // one byte per column; a step leaving the window is clamped (every read stays in this
+        // warp's rows) and recorded as a failure
+        const uint8_t *fb = reinterpret_cast<const uint8_t *>(fd) + (size_t)(re - 1 - rs) * FILLW;
+        for (int i = re - 1; i >= first; --i, fb -= FILLW) {
+          const int nr = rel + (int)fb[rel] - 1;
+          path[(i - rs) * PST] = (uint32_t)rel;   // the first 4 bytes of row i's direction words
+          okp &= (unsigned)nr < (unsigned)FILLW;
+          rel = min(max(nr, 0), FILLW - 1);
+        }
+      } else {
+        for (int i = re - 1; i >= first; --i) {
+          if (rel < 0 || rel >= FILLW) { okp = false; break; }
+          const uint32_t dd = ((uint32_t)fd[(i - rs) * 32 + rel / FV] >> (2 * (rel % FV))) & 3u;
+          path[(i - rs) * PST] = (uint32_t)rel;   // the first 4 bytes of row i's direction words
+          rel += (int)dd - 1;
+        }
+      }
+      if (!okp) {
+        atomicOr(errw, ERR_FILL_MISMATCH);
+        rel = -1 - x0;
+      }
+      path[KSS * PST - 1] = (uint32_t)rel;    // the column above row `first` (row 0's seam when s == 0)
+      if (x0 + rel != jprev) atomicOr(errw, ERR_FILL_MISMATCH);
+    }
+    __syncwarp();
+    const bool path_ok = (int)path[KSS * PST - 1] + x0 >= 0;
+    if (path_ok) {
+      for (int i = first + lane; i < re; i += 32) {
+        const int j = x0 + (int)path[(i - rs) * PST];
+        seam_out[i] = j;
+        if (seam_log) seam_log[i] = j;
+      }
+      if (s == 0 && lane == 0) {
+        const int j = x0 + (int)path[KSS * PST - 1];
+        seam_out[0] = j;
+        if (seam_log) seam_log[0] = j;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// backtrack_fill as a function of its own (not inlined): it gets its own register allocation, so
+// the one-CTA batched kernel, whose 512 threads have at most 128 registers each, can load deeper
+// energy chunks
+template <int NW, int KT, bool CL, int FWM, bool FWD, int KSS, bool DIRECT, int CH>
+static __device__ __noinline__ void backtrack_fill_call(FillCtx f, int warp, int lane) {
+  backtrack_fill<NW, KT, CL, FWM, FWD, KSS, DIRECT, CH>(f, warp, lane);
+}
+
 template <int NW, int KT, bool CL, int FWM = FILL_WARPS_MAX, bool FWD = false, int KSS = KS, bool DIRECT = false>
 __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, SearchState &st) {
   static_assert(!DIRECT || (CL && !FWD), "the in-place form is built for the cluster search of e1 maps");
@@ -593,197 +811,26 @@ __device__ void seam_search(const SearchArgs &p, unsigned char *smem, int Smax, 
   group_sync<CL>();
 
   // ---- parallel backtrack: each super-tile recomputed in a FILLW-column window ----
-  // A path cell r rows into a super-tile lies within KSS - 1 - r columns of the bottom column
-  // jb[s], and its three predecessors depend on the saved row only within KSS columns of jb[s]:
-  // the window [x0, x0 + FILLW) with x0 = jb[s] - FILLW / 2 (rounded down to FV) holds them all.
-  constexpr int FV = G::FV, FILLW = G::FILLW;
-  // direction rows: 2 bits per column (FV = 8), or one byte per column (FV = 4: the walk then
-  // reads its column's byte directly)
-  using DirT = typename std::conditional<FV == 8, uint16_t, uint32_t>::type;
-  using EVec = typename std::conditional<FV == 8, uint4, uint2>::type;        // FV uint16 energies
-  constexpr int PST = 32 * (int)sizeof(DirT) / 4;   // 32-bit words per direction row
   const int *jb0 = CL ? cg::this_cluster().map_shared_rank(jb, 0) : jb;
   const int *misc0 = CL ? cg::this_cluster().map_shared_rank(misc, 0) : misc;
   const int ok = misc0[0];
   const uint32_t best_m = (uint32_t)misc0[1];
-  DirT *fd = reinterpret_cast<DirT *>(fdir) + (size_t)warp * KSS * 32;
-  const uint16_t *const Ef = p.E;
-  int32_t *const seam_out = p.seam;
-  int32_t *const seam_log = p.seam_log;
-  int *const errw = p.err;
-  // the energies of a super-tile's window (KSS rows, two rows per lane at most) are prefetched
-  // into L2 one super-tile ahead: the map has usually left L2 since the DP pass read it. The
-  // prefetch starts on a 16-byte boundary and covers the window.
-  auto prefetch_window = [&](int s) {
-    if (s >= S) return;
-    int x0 = jb0[s] - FILLW / 2;
-    x0 -= ((x0 % 8) + 8) % 8;
-    int x1 = x0 + FILLW + 8;
-    if (DIRECT) {   // only the caller's columns
-      x0 = max(x0, 0);
-      x1 = min(x1, Wa);
-      if (x1 <= x0) return;
-    }
-    for (int i = s * KSS + lane; i < s * KSS + KSS && i < H; i += 32)
-#pragma unroll
-      for (int pl = 0; pl < NP; ++pl)
-        bulk_prefetch_l2(Ef + pl * pstride + (size_t)i * pitch_e + x0, (uint32_t)(x1 - x0) * 2);
-  };
-  auto unpack = [](const EVec &v, uint32_t (&x)[FV]) {
-    const uint32_t *w = reinterpret_cast<const uint32_t *>(&v);
-#pragma unroll
-    for (int q = 0; q < FV / 2; ++q) {
-      x[2 * q] = w[q] & 0xFFFFu;
-      x[2 * q + 1] = w[q] >> 16;
-    }
-  };
-  if (ok && warp < G::FW) prefetch_window(warp * cs + rank);
-  for (int s = warp * cs + rank; ok && warp < G::FW && s < S; s += G::FW * cs) {
-    prefetch_window(s + G::FW * cs);
-    const int jbs = jb0[s];
-    const int jprev = (s > 0) ? jb0[s - 1] : jb0[S];
-    int x0 = jbs - FILLW / 2;
-    x0 -= ((x0 % FV) + FV) % FV;
-    const int xc = x0 + lane * FV;
-    const int rs = s * KSS, re = (rs + KSS < H) ? rs + KSS : H;
-    const int first = (s == 0) ? 1 : rs;
-    uint32_t m[FV], oob[FV];
-#pragma unroll
-    for (int u = 0; u < FV; ++u) oob[u] = (xc + u < 0 || xc + u >= W) ? SENT : 0u;
-    // DIRECT: a lane's FV columns lie wholly inside or wholly outside the caller's [0, Wa)
-    const bool xin = !DIRECT || (xc >= 0 && xc + FV <= Wa);
-    if (s == 0) {
-      EVec v0{};
-      if (xin) v0 = *reinterpret_cast<const EVec *>(Ef + xc);
-      unpack(v0, m);
+  if (ok && warp < G::FW) {
+    const FillCtx f{p.E, Mrow, jb0, fdir, p.seam, p.seam_log, p.err, pstride, pitch_e, pitch_m, H, W, Wa, S, rank, cs,
+                    best_m};
+    // energy chunks: the single-map search (all fill warps, one CTA per SM, latency-bound) has
+    // registers to spare for chunks whose compute covers an L2 round trip (16 rows of 4 columns per
+    // lane, 8 rows of 8); the multi-map and cluster batched kernels, whose latency other CTAs hide
+    // and whose registers are capped, use 4- or 2-row chunks; the one-CTA batched kernel calls the
+    // fill as a function of its own, with 4-row chunks (config 4: 46.9 -> 45.3 ms; the same call in
+    // the cluster batched kernel made its largest image 37.1 -> 46.1 ms, so that one stays inline).
+    constexpr int FV = G::FV;
+    if constexpr (!CL && !FWD) {
+      backtrack_fill_call<NW, KT, CL, FWM, FWD, KSS, DIRECT, 4>(f, warp, lane);
     } else {
-#pragma unroll
-      for (int q = 0; q < FV / 4; ++q) {
-        const uint4 a = *reinterpret_cast<const uint4 *>(Mrow + (size_t)s * pitch_m + xc + 4 * q);
-        m[4 * q] = a.x; m[4 * q + 1] = a.y; m[4 * q + 2] = a.z; m[4 * q + 3] = a.w;
-      }
+      constexpr int CH = FWD ? 2 : ((CL && FWM >= FILL_WARPS_MAX) ? (FV == 4 ? 16 : 8) : (CL && FV == 4 ? 4 : 2));
+      backtrack_fill<NW, KT, CL, FWM, FWD, KSS, DIRECT, CH>(f, warp, lane);
     }
-#pragma unroll
-    for (int u = 0; u < FV; ++u) m[u] |= oob[u];
-    // rows first..re-1 in chunks with the next chunk's energies loaded ahead. The single-map
-    // search (all fill warps, one CTA per SM, latency-bound) has registers to spare for chunks
-    // whose compute covers an L2 round trip (16 rows of 4 columns per lane, 8 rows of 8); the
-    // batched and multi-map kernels, whose latency other CTAs hide and whose registers are
-    // capped, use 2-row chunks.
-    constexpr int CH = FWD ? 2 : ((CL && FWM >= FILL_WARPS_MAX) ? (FV == 4 ? 16 : 8) : (CL && FV == 4 ? 4 : 2));
-    EVec eb0[NP][CH], eb1[NP][CH];
-    auto load_chunk = [&](EVec (&eb)[NP][CH], int rbeg) {
-#pragma unroll
-      for (int r = 0; r < CH; ++r) {
-        const int i = rbeg + r;
-#pragma unroll
-        for (int pl = 0; pl < NP; ++pl)
-          if (i < re) {
-            if (xin) eb[pl][r] = *reinterpret_cast<const EVec *>(Ef + pl * pstride + (size_t)i * pitch_e + xc);
-            else eb[pl][r] = EVec{};
-          }
-      }
-    };
-    auto run_chunk = [&](const EVec (&eb)[NP][CH], int rbeg) {
-#pragma unroll
-      for (int r = 0; r < CH; ++r) {
-        const int i = rbeg + r;
-        if (i >= re) break;
-        uint32_t ee[FV], dl[FV], dr[FV];
-#pragma unroll
-        for (int u = 0; u < FV; ++u) dl[u] = dr[u] = 0u;
-        unpack(eb[0][r], ee);
-        if (FWD) {
-          unpack(eb[NP > 1 ? 1 : 0][r], dl);
-          unpack(eb[NP > 2 ? 2 : 0][r], dr);
-        }
-        const uint32_t L = __shfl_up_sync(0xffffffffu, m[FV - 1], 1);
-        const uint32_t R = __shfl_down_sync(0xffffffffu, m[0], 1);
-        uint32_t nm[FV];
-        uint32_t dirs = 0;
-#pragma unroll
-        for (int u = 0; u < FV; ++u) {
-          const uint32_t a = ((u == 0) ? L : m[u - 1]) + dl[u];
-          const uint32_t b = m[u];
-          const uint32_t c = ((u == FV - 1) ? R : m[u + 1]) + dr[u];
-          const uint32_t mn = min3u(a, b, c);
-          const uint32_t dd = (a == mn) ? 0u : ((b == mn) ? 1u : 2u);
-          dirs |= dd << ((FV == 4 ? 8 : 2) * u);
-          nm[u] = add_mask<true>(mn, ee[u], oob[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < FV; ++u) m[u] = nm[u];
-        fd[(i - rs) * 32 + lane] = (DirT)dirs;
-      }
-    };
-    int rb = first;
-    load_chunk(eb0, rb);
-    while (rb < re) {
-      if (rb + CH < re) load_chunk(eb1, rb + CH);
-      run_chunk(eb0, rb);
-      rb += CH;
-      if (rb >= re) break;
-      if (rb + CH < re) load_chunk(eb0, rb + CH);
-      run_chunk(eb1, rb);
-      rb += CH;
-    }
-    if (s == S - 1) {
-      // the recomputed cost at the bottom of the seam must be the argmin's
-      const int rel = jbs - x0;
-      if (rel / FV == lane) {
-        uint32_t v = 0;
-#pragma unroll
-        for (int u = 0; u < FV; ++u) if (u == rel % FV) v = m[u];
-        if (v != best_m) atomicOr(errw, ERR_COST_MISMATCH);
-      }
-    }
-    __syncwarp();
-    // lane 0 follows the directions up the window (relative columns, kept in the direction rows it
-    // has read: a row's entry is not needed again), then the warp writes the seam rows
-    uint32_t *path = reinterpret_cast<uint32_t *>(fd);   // path[(i - rs) * PST] holds the column of row i
-    if (lane == 0) {
-      int rel = jbs - x0;
-      bool okp = true;
-      if constexpr (FV == 4) {
-        // one byte per column; a step leaving the window is clamped (every read stays in this
-        // warp's rows) and recorded as a failure
-        const uint8_t *fb = reinterpret_cast<const uint8_t *>(fd) + (size_t)(re - 1 - rs) * FILLW;
-        for (int i = re - 1; i >= first; --i, fb -= FILLW) {
-          const int nr = rel + (int)fb[rel] - 1;
-          path[(i - rs) * PST] = (uint32_t)rel;   // the first 4 bytes of row i's direction words
-          okp &= (unsigned)nr < (unsigned)FILLW;
-          rel = min(max(nr, 0), FILLW - 1);
-        }
-      } else {
-        for (int i = re - 1; i >= first; --i) {
-          if (rel < 0 || rel >= FILLW) { okp = false; break; }
-          const uint32_t dd = ((uint32_t)fd[(i - rs) * 32 + rel / FV] >> (2 * (rel % FV))) & 3u;
-          path[(i - rs) * PST] = (uint32_t)rel;   // the first 4 bytes of row i's direction words
-          rel += (int)dd - 1;
-        }
-      }
-      if (!okp) {
-        atomicOr(errw, ERR_FILL_MISMATCH);
-        rel = -1 - x0;
-      }
-      path[KSS * PST - 1] = (uint32_t)rel;    // the column above row `first` (row 0's seam when s == 0)
-      if (x0 + rel != jprev) atomicOr(errw, ERR_FILL_MISMATCH);
-    }
-    __syncwarp();
-    const bool path_ok = (int)path[KSS * PST - 1] + x0 >= 0;
-    if (path_ok) {
-      for (int i = first + lane; i < re; i += 32) {
-        const int j = x0 + (int)path[(i - rs) * PST];
-        seam_out[i] = j;
-        if (seam_log) seam_log[i] = j;
-      }
-      if (s == 0 && lane == 0) {
-        const int j = x0 + (int)path[KSS * PST - 1];
-        seam_out[0] = j;
-        if (seam_log) seam_log[0] = j;
-      }
-    }
-    __syncwarp();
   }
   group_sync<CL>();   // rank 0's shared memory is read above; the seam is complete after this
 }
