@@ -148,45 +148,43 @@ __device__ __forceinline__ int lazy_count(const LazyRow &r, int j) {
 // except at the new columns s_i - 1 and s_i (their left/right neighbour changed, and, since
 // |s_i - s_(i+-1)| <= 1, they are the only pixels whose upper/lower neighbour can change). They
 // are computed from the old image seen through the removal: new pixel (r, j) = old (r, j + [j >= s_r]).
-// Returns (e(s-1) | e(s) << 16); a value is 0 when its column does not exist. *bad is set when
-// the seam column is out of range. The image is read through the pending-removal lists `lists`
-// (row r at lists + r*RPEND, m entries each) of the width-W image the seam was found in; row i's
-// list comes back in *li for the insertion that follows.
-__device__ __forceinline__ uint32_t patch_row_lazy(const uint32_t *img, int pitch, int H, int W, const int32_t *seam,
-                                                   const int16_t *lists, int m, int i, bool *bad, LazyRow *li) {
+// Returns (e(s-1) | e(s) << 16); a value is 0 when its column does not exist. The image is read
+// through the pending-removal lists of the width-W image the seam was found in: lc is row i's (seam
+// column s), lu and ld those of the rows above and below, iu and id (edge rows replicated), whose
+// seam columns are su and sd.
+__device__ __forceinline__ uint32_t patch_pair(const uint32_t *img, int pitch, int W, int i, int s, int iu, int su,
+                                               const LazyRow &lu, const LazyRow &lc, int id, int sd,
+                                               const LazyRow &ld) {
   const int Wn = W - 1;
-  const int s = seam[i];
-  *li = lazy_row(lists + (int64_t)i * RPEND, m);
-  if (s < 0 || s >= W) {
-    *bad = true;
-    return 0u;
-  }
   // new pixel (r, j), j clamped to the new width, of a row r whose seam column is sr and list L
   auto pix = [&](int r, const LazyRow &L, int sr, int j) -> uint32_t {
     j = clampi(j, 0, Wn - 1);
     const int x = j + (j >= sr ? 1 : 0);                    // column in the width-W image
     return img[(int64_t)r * pitch + x + lazy_count(L, x)];
   };
-  // columns s-1 and s of the rows above and below (edge rows replicated), one row's list at a time
-  uint32_t up0, up1, dn0, dn1;
-  {
-    const int r = i > 0 ? i - 1 : 0;
-    const LazyRow L = lazy_row(lists + (int64_t)r * RPEND, m);
-    const int sr = seam[r];
-    up0 = pix(r, L, sr, s - 1);
-    up1 = pix(r, L, sr, s);
-  }
-  {
-    const int r = i + 1 < H ? i + 1 : H - 1;
-    const LazyRow L = lazy_row(lists + (int64_t)r * RPEND, m);
-    const int sr = seam[r];
-    dn0 = pix(r, L, sr, s - 1);
-    dn1 = pix(r, L, sr, s);
-  }
-  const LazyRow &lc = *li;
+  // columns s-1 and s of the rows above and below (edge rows replicated)
+  const uint32_t up0 = pix(iu, lu, su, s - 1), up1 = pix(iu, lu, su, s);
+  const uint32_t dn0 = pix(id, ld, sd, s - 1), dn1 = pix(id, ld, sd, s);
   const uint32_t p0 = (s >= 1) ? sad4(pix(i, lc, s, s), pix(i, lc, s, s - 2)) + sad4(dn0, up0) : 0u;
   const uint32_t p1 = (s <= Wn - 1) ? sad4(pix(i, lc, s, s + 1), pix(i, lc, s, s - 1)) + sad4(dn1, up1) : 0u;
   return p0 | (p1 << 16);
+}
+
+// patch_pair of row i, its seam columns and lists read here (lists: row r at lists + r*RPEND, m
+// entries each); row i's list comes back in *li for the insertion that follows, and *bad is set
+// when the seam column is out of range.
+__device__ __forceinline__ uint32_t patch_row_lazy(const uint32_t *img, int pitch, int H, int W, const int32_t *seam,
+                                                   const int16_t *lists, int m, int i, bool *bad, LazyRow *li) {
+  const int s = seam[i];
+  *li = lazy_row(lists + (int64_t)i * RPEND, m);
+  if (s < 0 || s >= W) {
+    *bad = true;
+    return 0u;
+  }
+  const int iu = i > 0 ? i - 1 : 0, id = i + 1 < H ? i + 1 : H - 1;
+  const LazyRow lu = lazy_row(lists + (int64_t)iu * RPEND, m);
+  const LazyRow ld = lazy_row(lists + (int64_t)id * RPEND, m);
+  return patch_pair(img, pitch, W, i, s, iu, seam[iu], lu, *li, id, seam[id], ld);
 }
 
 // Add a row's removal at current column s to its sorted list (L: the row's m entries): the removals
@@ -276,6 +274,18 @@ namespace sc {
 __device__ __forceinline__ bool refresh_row(const uint32_t *img, int pitch, uint16_t *E, int pe, int H, int W,
                                             const int32_t *seam, const int16_t *lists_in, int16_t *lists_out, int m,
                                             int i, int lane) {
+  // lane 0's pending-removal lists of rows i-1, i, i+1 and the neighbours' seam columns depend on i
+  // alone: loaded beside seam[i], they take a round trip off the refreshed pair's path
+  const int iu = i > 0 ? i - 1 : 0, id = i + 1 < H ? i + 1 : H - 1;
+  LazyRow lu{}, lc{}, ld{};
+  int su = 0, sd = 0;
+  if (lane == 0) {
+    lc = lazy_row(lists_in + (int64_t)i * RPEND, m);
+    lu = lazy_row(lists_in + (int64_t)iu * RPEND, m);
+    ld = lazy_row(lists_in + (int64_t)id * RPEND, m);
+    su = seam[iu];
+    sd = seam[id];
+  }
   const int s = seam[i];
   if (s < 0 || s >= W) return false;
   uint32_t p = 0;
@@ -284,10 +294,8 @@ __device__ __forceinline__ bool refresh_row(const uint32_t *img, int pitch, uint
   // the warp's loads of the energy tail are in flight
   shift_row_u16(er, s, W, lane, [&] {
     if (lane == 0) {
-      bool bad = false;
-      LazyRow li;
-      p = patch_row_lazy(img, pitch, H, W, seam, lists_in, m, i, &bad, &li);
-      list_insert(li, lists_out + (int64_t)i * RPEND, s);
+      p = patch_pair(img, pitch, W, i, s, iu, su, lu, lc, id, sd, ld);
+      list_insert(lc, lists_out + (int64_t)i * RPEND, s);
     }
   });
   if (lane == 0) {
