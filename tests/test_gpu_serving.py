@@ -93,3 +93,21 @@ def test_request_completes_with_its_own_image(dev):
     for im, t in zip(smalls, ts):
         np.testing.assert_array_equal(srv.result(t), oracle.carve(im, im.shape[1] - 10, im.shape[0]))
     srv.close()
+
+
+def test_heavy_narrow_request_goes_to_a_cluster(dev):
+    """A request one CTA covers (600 columns) but whose carve there would take well over 50 ms by the
+    carving-time model (2000 rows, 300 seams) is carved by a latency-shaped cluster; a light one
+    stays on one CTA. Both equal the oracle's carve."""
+    heavy = synth.gen_image(600, 2000, 12, 20, 200, 91)
+    light = synth.gen_image(300, 200, 4, 10, 60, 92)
+    srv = sc.Server(budget_bytes=1 << 30, max_batch=8, streams=2)
+    th_ = srv.submit(heavy, 300, 2000)
+    tl = srv.submit(light, 250, 200)
+    srv.drain(300)
+    st = srv.stats()
+    assert st["completed"] == 2 and st["device_errors"] == 0
+    assert st["cluster_path"] == 1 and st["batched"] == 1, st
+    np.testing.assert_array_equal(srv.result(th_), oracle.carve(heavy, 300, 2000))
+    np.testing.assert_array_equal(srv.result(tl), oracle.carve(light, 250, 200))
+    srv.close()
