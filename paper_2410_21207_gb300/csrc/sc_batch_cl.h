@@ -9,9 +9,10 @@ constexpr size_t BATCH_CL_SMEM_MAX = 232448 - 1024;   // the opt-in limit minus 
 // Two cluster shapes of the persistent kernel:
 //   CL_WIDE: 8 compute warps, 8-row tiles, 768 own columns per CTA. Images wider than one CTA of the
 //            one-CTA kernel: few CTAs per image, little redundant halo work (throughput).
-//   CL_LAT:  8 compute warps, 32-row tiles, 384 own columns per CTA. The heaviest images of a batch:
-//            a quarter of the tile boundaries per seam and twice the CTAs, so one image's seams
-//            finish sooner (latency), at more SM time per seam.
+//   CL_LAT:  8 compute warps, 32-row tiles, 384 own columns per CTA. The heaviest images of a
+//            batch, and the serving form's wide and heavy requests: a quarter of the tile boundaries
+//            per seam and twice the CTAs, so one image's seams finish sooner (latency), at more SM
+//            time per seam.
 enum ClShape { CL_WIDE = 0, CL_LAT = 1 };
 
 struct ClOps {

@@ -145,7 +145,7 @@ def test_balanced_plan_runs_clusters_beside_one_cta_kernel(dev):
 
 
 def test_balanced_plan_several_cluster_groups(dev):
-    """Three cluster groups beside the one-CTA kernel, each on its own stream: two heavy images of
+    """Three cluster groups chained ahead of the one-CTA kernel: two heavy images of
     different widths on 32-row-tile clusters (1000 columns: 3 CTAs, 600 columns: 2 CTAs), one image
     wider than a CTA (1700 columns) on the 8-row-tile shape, and small images on one CTA each; two
     passes for one heavy image. Every image equals the oracle's carve of it alone, on two replays."""
