@@ -911,9 +911,8 @@ static int batch_prepare(BatchRun &r, const sc_image_desc *descs, int n, const B
   // x per_sm when CTAs share an SM), a group's images on its clusters (estimated time on a cluster
   // of its shape and size). For every end time T a group can reach, each group takes the fewest
   // clusters that end by T and the one-CTA images the SMs left over; the T whose batch ends first
-  // wins. At least one
-  // cluster per group, never more than resident at once or than the group has images; the one-CTA
-  // launch keeps at least one SM.
+  // wins. At least one cluster per group, never more than resident at once (on an otherwise idle
+  // GPU) or than the group has images; the one-CTA launch keeps at least one SM.
   r.cl_clusters.assign(ng, 1);
   std::vector<double> t1;
   for (const BatchItem &it : r.setup.items) t1.push_back(batch_item_us(it, cost_one_cta()) * per_sm);
