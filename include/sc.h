@@ -275,6 +275,21 @@ int sc_carve_batch(const sc_image_desc *descs, int n, void *stream);
  * change between runs; their pointers and sizes may not. sc_batch_plan_run enqueues one replay on
  * `stream`; sc_batch_plan_info reports the chosen configuration (compute warps, tile height, CTAs
  * launched, images carved by one CTA / by one cluster each). */
+/* The routing a batch plan applies, computed on the host with no device call (the paper has no
+ * counterpart: this is the batched form's scheduler, exposed so that callers can see where their
+ * images go). descs: HOST array of n descriptors (only H, W, C, target_w and target_h are read;
+ * the pointers may be NULL); thr: the balancing threshold (images whose estimated one-CTA carve
+ * exceeds thr x the batch's mean share per SM go to clusters of the 32-row-tile shape; 0: no
+ * balancing; autotune = 2 uses 1.4); sms: the SM count the share is computed over (152 on a
+ * GB300). Outputs, HOST arrays of n: cluster_size[k] 0 when one CTA carves image k, the cluster's
+ * CTA count otherwise, -1 when no cluster covers it (the per-seam path carves it); shape[k] 0 for
+ * clusters of 8-row tiles (images wider than one CTA), 1 for clusters of 32-row tiles; one_cta_us
+ * (nullable): the carving-time model's estimate of image k's carve on one CTA, in microseconds.
+ * Errors: SC_EINVAL for a NULL array, n < 1, thr < 0, sms < 1 or a descriptor that fails the
+ * sc_carve size checks. */
+int sc_batch_route(const sc_image_desc *descs, int n, float thr, int sms, int *cluster_size, int *shape,
+                   double *one_cta_us);
+
 typedef struct sc_batch_plan sc_batch_plan;
 int sc_batch_plan_create(const sc_image_desc *descs, int n, int autotune, void *stream, sc_batch_plan **plan);
 int sc_batch_plan_run(sc_batch_plan *plan, void *stream);

@@ -64,6 +64,7 @@ def load(path: Optional[str] = None):
                 "sc_find_seam_static": ([P, I, I, P, P, P], I),
                 "sc_find_seam_static_selftest": ([I, I, P, P, P], I),
                 "sc_find_seam_multi": ([P, I, I, I, P, P, P], I),
+                "sc_batch_route": ([P, I, ctypes.c_float, I, P, P, P], I),
                 "sc_greedy_seam": ([P, I, I, P, P, P], I),
                 "sc_enlarge": ([P, I, I, I, I, P, P, P], I),
                 "sc_selftest_wait_timeout": ([I, P], I),
@@ -401,6 +402,22 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+def batch_route(sizes, thr: float = 1.4, sms: int = 152):
+    """sc_batch_route: where a batch plan carves each image, computed on the host (no device call).
+    sizes: (H, W, C, target_w, target_h) per image -> (cluster_size, shape, one_cta_us) lists:
+    cluster_size 0 for one CTA, the cluster's CTA count, or -1 for the per-seam path; shape 0 for
+    8-row-tile clusters, 1 for 32-row-tile clusters; one_cta_us the model's one-CTA carve time."""
+    n = len(sizes)
+    descs = (ImageDesc * max(n, 1))()
+    for k, (H, W, C, tw, th) in enumerate(sizes):
+        descs[k].H, descs[k].W, descs[k].C, descs[k].target_w, descs[k].target_h = H, W, C, tw, th
+    cs = (ctypes.c_int * max(n, 1))()
+    sh = (ctypes.c_int * max(n, 1))()
+    us = (ctypes.c_double * max(n, 1))()
+    _raise(load().sc_batch_route(ctypes.cast(descs, ctypes.c_void_p), n, ctypes.c_float(thr), int(sms), cs, sh, us))
+    return list(cs)[:n], list(sh)[:n], list(us)[:n]
 
 
 def probe_copy_bandwidth(nbytes: int, reps: int) -> float:

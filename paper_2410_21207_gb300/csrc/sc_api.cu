@@ -755,7 +755,7 @@ void batch_layout(const sc_image_desc *descs, int n, const BatchCfg &c, unsigned
   // not when the largest image does)
   std::vector<char> bal(n, 0);
   if (c.thr_bal > 0.f) {
-    const int sms = device_sms();
+    const int sms = c.sms > 0 ? c.sms : device_sms();
     double total = 0.0;
     for (int k = 0; k < n; ++k) total += item_us(descs[k], cost_one_cta());
     const double share = sms > 0 ? total / sms : 0.0;
@@ -1121,6 +1121,35 @@ int sc_batch_plan_run(sc_batch_plan *plan, void *stream) {
     int rc = carve_impl(d.img, d.H, d.W, d.C, d.target_w, d.target_h, d.out, d.seam_log, nullptr, st);
     if (rc) return rc;
   }
+  return SC_OK;
+}
+
+int sc_batch_route(const sc_image_desc *descs, int n, float thr, int sms, int *cluster_size, int *shape,
+                   double *one_cta_us) {
+  if (!descs || n < 1 || !cluster_size || !shape) return fail(SC_EINVAL, "empty batch or null output");
+  if (!(thr >= 0.f) || sms < 1) return fail(SC_EINVAL, "need thr >= 0 and sms >= 1");
+  for (int k = 0; k < n; ++k) {
+    const sc_image_desc &d = descs[k];
+    // only the sizes matter here: the descriptor's own address stands in for the image pointers
+    const int rc = check_carve_args(&d, d.H, d.W, d.C, d.target_w, d.target_h, &d);
+    if (rc) return fail(rc, "descriptor %d: %s", k, g_last_error.c_str());
+  }
+  BatchCfg c = default_batch_cfg(descs, n);
+  c.thr_bal = thr;
+  c.sms = sms;
+  BatchSetup b;
+  batch_layout(descs, n, c, nullptr, b);
+  for (int k = 0; k < n; ++k) {
+    cluster_size[k] = 0;
+    shape[k] = CL_WIDE;
+    if (one_cta_us) one_cta_us[k] = item_us(descs[k], cost_one_cta());
+  }
+  for (const ClusterGroup &g : b.cl)
+    for (int k : g.index) {
+      cluster_size[k] = g.cs;
+      shape[k] = g.shape;
+    }
+  for (int k : b.fallback) cluster_size[k] = -1;
   return SC_OK;
 }
 

@@ -33,6 +33,8 @@ struct BatchCfg {
   // images whose estimated carving time on one CTA exceeds lat_us microseconds take the latency
   // shape as well (0: off): the serving form's heaviest narrow requests
   float lat_us = 0.f;
+  // SMs the balancing share is computed over (0: the current device's)
+  int sms = 0;
 };
 // images carved by the cluster-per-image batched kernel: those wider than one CTA (CL_WIDE
 // shape) and the heaviest ones of a balanced plan (CL_LAT); one group per shape and cluster size
