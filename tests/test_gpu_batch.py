@@ -165,3 +165,25 @@ def test_balanced_plan_several_cluster_groups(dev):
         sc.check()
         _check(imgs, targets, plan.outs, plan.logs)
     plan.close()
+
+
+def test_route_query_matches_the_balanced_plan(dev):
+    """sc_batch_route (host only) predicts the plan's routing: a balanced plan (autotune = 2, the
+    1.4 threshold) of the first 96 config-4 images carves on clusters exactly as many images as the
+    query sends to clusters for this device's SM count, and every image still equals the oracle."""
+    jobs = synth.config4()[:96]
+    imgs = [j.make() for j in jobs]
+    targets = [(j.target_w, j.target_h) for j in jobs]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    cs, shape, us = sc.batch_route([(j.H, j.W, 3, j.target_w, j.target_h) for j in jobs], 1.4, sms)
+    routed = sum(1 for c in cs if c > 0)
+    assert routed > 0
+    d = [torch.from_numpy(i).to(dev) for i in imgs]
+    plan = sc.BatchPlan(d, targets, autotune=2, with_log=True)
+    info = plan.info()
+    assert info["cluster_path"] == routed and info["batched"] == len(jobs) - routed, (info, routed)
+    plan.run()
+    sc.check()
+    for k in range(0, len(jobs), 12):   # a sample against the oracle (the whole batch is in the full-size test)
+        _check([imgs[k]], [targets[k]], [plan.outs[k]], [plan.logs[k]])
+    plan.close()
