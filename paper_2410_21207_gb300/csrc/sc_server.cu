@@ -114,6 +114,7 @@ struct Request {
   bool staged = false;                              // out is pageable: the result goes through staging
   size_t hoff = 0, hbytes = 0;                      // staging block
   int flag = -1;                                    // index of the completion word
+  int kind = 0;                                     // kind_of at submission (sizes and config fixed)
   std::vector<std::pair<size_t, size_t>> dallocs;   // device arena blocks (offset, bytes)
 };
 
@@ -245,7 +246,7 @@ void retire(sc_server *s) {
 // Start one micro-batch if possible (caller holds the lock). Returns true if something was launched.
 bool admit(sc_server *s) {
   if (s->queue.empty() || s->streams.empty() || s->free_events.empty() || s->free_flags.size() < 2) return false;
-  const int kind = kind_of(s, s->reqs[s->queue.front()]);
+  const int kind = s->reqs[s->queue.front()].kind;
   std::vector<int64_t> take;
   std::vector<sc_image_desc> descs;
   std::vector<std::pair<size_t, size_t>> allocs;
@@ -253,7 +254,7 @@ bool admit(sc_server *s) {
   for (int64_t tk : s->queue) {
     if ((int)take.size() >= s->max_batch) break;
     Request &r = s->reqs[tk];
-    if (kind_of(s, r) != kind) continue;   // another kind's micro-batch takes it
+    if (r.kind != kind) continue;   // another kind's micro-batch takes it
     sc_image_desc d = desc_of(r);
     int S = 1;
     const size_t scratch = item_bytes(s, d, &S);
@@ -457,6 +458,7 @@ int sc_server_submit(sc_server *s, const uint8_t *img_host, int H, int W, int C,
   int S = 1;
   const size_t need = (size_t)H * W * C + (size_t)target_h * target_w * C + item_bytes(s, desc_of(r), &S) + 4096;
   if (need > s->arena.size) return fail(SC_ENOMEM, "a %d x %d request needs more than the whole budget", W, H);
+  r.kind = kind_of(s, r);
   std::lock_guard<std::mutex> lk(s->mu);
   const int64_t t = s->next_ticket++;
   s->reqs[t] = r;
